@@ -1,0 +1,392 @@
+#!/usr/bin/env python3
+"""Benchmark of the P-HGRMS denoiser on GB300.
+
+Workload (default): one seeded 8192 x 8192 uint8 image (smooth content, 30 %
+salt-and-pepper noise), alpha = 10, denoised with beta = 1, 2 and 3, each up
+to max_k = 32 passes.  One step = the three denoising calls (the whole
+workload).  Metric: Mpixel-iter/s = sum over the calls of rows*cols*k
+divided by the step time; every call's output is bit-identical to the CPU
+oracle (checked by the GPU parity tests on this same configuration).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank denoises its own copy of the workload on its own
+GPU (independent images, no collective in the data path: weak scaling);
+rank 0 prints one JSON line.  ``--impl reference`` times the CPU oracle on a
+bounded sample of the same workload (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel-iter/s bit-exact vs oracle"
+UNIT = "Mpixel-iter/s"
+L2_FLUSH_BYTES = 256 << 20
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    p.add_argument("--workload", choices=("8192", "256"), default="8192")
+    p.add_argument("--betas", default="1,2,3")
+    p.add_argument("--passes", type=int, default=0, help="fused passes per launch (0 = built-in)")
+    p.add_argument("--kernel", type=int, default=0, help="0 fused, 1 unfused")
+    p.add_argument("--size", type=int, default=8192, help="side of the square image (8192 workload)")
+    p.add_argument("--cpu-rows", type=int, default=128, help="rows of the oracle baseline sample")
+    p.add_argument("--ref-rows", type=int, default=64, help="rows of each reference-arm step")
+    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args(argv)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", str(rank)))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def workload(args):
+    from paper_1306_5390_gb300 import synth
+    betas = [int(b) for b in args.betas.split(",")]
+    if args.workload == "256":
+        w = synth.workload_256()
+        return dict(name="256x256 uint8, 10% salt-and-pepper, alpha 10, beta 1, max_k 32",
+                    noisy=w["noisy"], alpha=10, betas=[1], max_k=32)
+    w = synth.workload_8192(1, size=args.size)
+    bl = ",".join(str(b) for b in betas)
+    return dict(name=f"{args.size}x{args.size} uint8, 30% salt-and-pepper, alpha 10, beta {{{bl}}}, max_k 32",
+                noisy=w["noisy"], alpha=10, betas=betas, max_k=32)
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.file = None
+
+    def start(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.file.flush()
+        self.file.seek(0)
+        rows = [ln.strip().split(",") for ln in self.file if ln.strip()]
+        self.file.close()
+        os.unlink(self.file.name)
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# our arm
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_1306_5390_gb300 import build, hgrms
+
+    build.build()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    w = workload(args)
+    rows, cols = w["noisy"].shape
+    betas, alpha, max_k = w["betas"], w["alpha"], w["max_k"]
+    src = torch.from_numpy(w["noisy"]).cuda()
+    work = [torch.empty_like(src) for _ in betas]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    d = hgrms.Denoiser(local, kernel=args.kernel, passes=args.passes, timing=True)
+
+    def step(per_beta):
+        for i, b in enumerate(betas):
+            k = d.denoise(work[i], alpha, b, max_k)
+            st = d.stats()
+            per_beta[b]["k"] = k
+            per_beta[b]["converged"] = d.converged()
+            for key in ("kernel_ms", "idle_kernel_ms"):
+                per_beta[b][key] += st[key]
+            for key in ("work_launches", "launches", "passes_executed"):
+                per_beta[b][key] += st[key]
+            per_beta[b]["T"] = st["passes_per_launch"]
+            per_beta[b]["ctas"] = st["ctas_per_launch"]
+            per_beta[b]["calls"] += 1
+
+    def fresh():
+        for t in work:
+            t.copy_(src)
+        flush.zero_()
+        torch.cuda.synchronize()
+
+    def new_acc():
+        return {b: dict(k=0, converged=False, kernel_ms=0.0, idle_kernel_ms=0.0, work_launches=0, launches=0,
+                        passes_executed=0, T=0, ctas=0, calls=0) for b in betas}
+
+    for _ in range(args.warmup):
+        fresh()
+        step(new_acc())
+    acc = new_acc()
+    clocks = ClockSampler(local)
+    clocks.start()
+    total_ms = 0.0
+    units = 0
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    for _ in range(args.steps):
+        fresh()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0.record()
+        step(acc)
+        ev1.record()
+        torch.cuda.synchronize()
+        total_ms += ev0.elapsed_time(ev1)
+        units += sum(rows * cols * acc[b]["k"] for b in betas)
+    clk = clocks.stop()
+    if dist is not None:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        u = torch.tensor([units], dtype=torch.float64, device="cuda")
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        units = int(u.item())
+    value = units / (total_ms * 1e-3) / 1e6
+
+    # End to end: host (pinned) image in, host image out, through the C ABI.
+    pinned = [torch.empty((rows, cols), dtype=torch.uint8).pin_memory() for _ in betas]
+    host_np = [p.numpy() for p in pinned]
+    e2e_s = 0.0
+    e2e_units = 0
+    for _ in range(args.e2e_steps):
+        for hn in host_np:
+            hn[...] = w["noisy"]
+        if dist is not None:
+            dist.barrier()
+        t0 = time.perf_counter()
+        ks = [d.denoise(host_np[i], alpha, b, max_k) for i, b in enumerate(betas)]
+        e2e_s += time.perf_counter() - t0
+        e2e_units += sum(rows * cols * k for k in ks)
+    if dist is not None:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+        u = torch.tensor([e2e_units], dtype=torch.float64, device="cuda")
+        dist.all_reduce(u, op=dist.ReduceOp.SUM)
+        e2e_units = int(u.item())
+    e2e_value = e2e_units / e2e_s / 1e6 if e2e_s > 0 else None
+
+    peaks, peak_kind = measured_peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    per_beta_out = {}
+    dom_b, dom_ms = None, -1.0
+    for b in betas:
+        a = acc[b]
+        taps = (2 * b + 1) ** 2 - 1
+        tests = taps * rows * cols * a["passes_executed"]
+        per_beta_out[str(b)] = dict(
+            k=a["k"], converged=bool(a["converged"]), passes_per_launch=a["T"],
+            work_launches_per_call=a["work_launches"] / max(1, a["calls"]),
+            kernel_ms_per_call=a["kernel_ms"] / max(1, a["calls"]),
+            idle_launch_ms_per_call=a["idle_kernel_ms"] / max(1, a["calls"]),
+            neighbour_tests_per_s=tests / (a["kernel_ms"] * 1e-3) if a["kernel_ms"] > 0 else None,
+            mpix_iter_per_s=rows * cols * a["k"] * a["calls"] / (a["kernel_ms"] * 1e-3) / 1e6
+            if a["kernel_ms"] > 0 else None)
+        if a["kernel_ms"] > dom_ms:
+            dom_b, dom_ms = b, a["kernel_ms"]
+    a = acc[dom_b]
+    taps = (2 * dom_b + 1) ** 2 - 1
+    tests_per_launch = taps * rows * cols * a["passes_executed"] / max(1, a["work_launches"])
+    launch_s = a["kernel_ms"] * 1e-3 / max(1, a["work_launches"])
+    achieved = tests_per_launch / launch_s / 1e9
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = sms * 128 * sm_mhz * 1e6 / 1e9
+    roofline = {
+        "bound": "alu",
+        "kernel": f"fused_kernel<beta={dom_b},T={a['T']}>",
+        "achieved": round(achieved, 1),
+        "peak": round(alu_peak, 1),
+        "unit": "Gtest/s",
+        "frac": round(achieved / alu_peak, 4),
+        "traffic": traffic_from_profiles(dom_b, a["T"], rows, cols),
+        "algorithmic_unit": f"one neighbour comparison of Algorithm 1/2: {taps} per pixel per pass",
+        "peak_basis": f"{sms} SMs x 128 lanes x {sm_mhz:.0f} MHz ({peak_kind} sm_max_mhz)",
+        "launch_ms": round(launch_s * 1e3, 4),
+    }
+    pix_iters_per_step = units / max(1, args.steps) / world
+    step_s = total_ms * 1e-3 / args.steps
+    hbm_eff = 2.0 * pix_iters_per_step / step_s / 1e9
+    launches = sum(acc[b]["launches"] + 3 * acc[b]["calls"] for b in betas)
+
+    out = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded Gaussian-bump + gradient content, salt-and-pepper noise)",
+        "config": {"workload": w["name"], "parallelism": f"replicas{world}" if world > 1 else "single",
+                   "l2": f"{L2_FLUSH_BYTES >> 20} MiB buffer written before every timed step",
+                   "kernel": "unfused" if args.kernel else "fused", "rows": rows, "cols": cols},
+        "roofline": roofline,
+        "hbm_effective": {"bytes_per_pixel_iter": 2, "achieved_gbs": round(hbm_eff, 1),
+                          "peak_gbs": peaks.get("hbm_gbs"), "frac": round(hbm_eff / peaks.get("hbm_gbs", 6800.0), 4),
+                          "peak_kind": peak_kind},
+        "per_beta": per_beta_out,
+        "e2e": {"value": round(e2e_value, 1) if e2e_value else None, "unit": UNIT,
+                "h2d_bytes_per_step": rows * cols * len(betas), "d2h_bytes_per_step": rows * cols * len(betas),
+                "steps": args.e2e_steps, "timer": "host perf_counter around the C-ABI calls on pinned host images"},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(w, args.cpu_rows)
+    d.close()
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
+def traffic_from_profiles(beta, T, rows, cols):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu
+    summary (profiles/fused_b{beta}_t{T}.txt, line 'dram_bytes_per_launch:'),
+    or None when no capture of the current kernel exists."""
+    path = os.path.join(ROOT, "profiles", f"fused_b{beta}_t{T}_{rows}x{cols}.txt")
+    if not os.path.exists(path):
+        return None
+    for ln in open(path):
+        if ln.startswith("dram_bytes_per_launch:"):
+            try:
+                return int(float(ln.split(":", 1)[1].split()[0]))
+            except ValueError:
+                return None
+    return None
+
+
+def oracle_sample(w, band_rows):
+    import oracle
+    oracle.build()
+    band = np.ascontiguousarray(w["noisy"][:band_rows])
+    units = 0
+    t0 = time.perf_counter()
+    for b in w["betas"]:
+        _, k, _ = oracle.denoise(band, w["alpha"], b, w["max_k"])
+        units += band.shape[0] * band.shape[1] * k
+    return units, time.perf_counter() - t0, band.shape
+
+
+def cpu_baseline(w, band_rows):
+    units, secs, shape = oracle_sample(w, band_rows)
+    return {"value": round(units / secs / 1e6, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"rows 0-{shape[0] - 1} of the same image ({shape[0]}x{shape[1]}), "
+                      f"beta {w['betas']}, max_k {w['max_k']}, single-threaded C oracle, {secs:.1f} s"}
+
+
+# --------------------------------------------------------------------------
+# reference arm: the CPU oracle on a bounded sample of the same workload
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = workload(args)
+    rows = min(args.ref_rows, w["noisy"].shape[0])
+    for _ in range(args.warmup):
+        oracle_sample(w, rows)
+    units = 0
+    secs = 0.0
+    shape = None
+    for _ in range(args.steps):
+        u, s, shape = oracle_sample(w, rows)
+        units += u
+        secs += s
+    value = units / secs / 1e6
+    sample = (f"rows 0-{shape[0] - 1} of the workload image ({shape[0]}x{shape[1]}), beta {w['betas']}, "
+              f"max_k {w['max_k']}, per step")
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(secs * 1e3 / args.steps, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded Gaussian-bump + gradient content, salt-and-pepper noise)",
+        "config": {"workload": w["name"], "parallelism": "single"},
+        "impl": "reference",
+        "cpu_baseline": {"value": round(value, 3), "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": round(value, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,137 @@
+/*
+ * hgrms.h - C ABI of the GB300 P-HGRMS salt-and-pepper denoiser.
+ *
+ * The method (P-HGRMS, Sections 2 and 3 of the paper):
+ *   For an 8-bit greyscale image I (rows x cols, row-major I[r*cols + c]),
+ *   parameters alpha (grey-level tolerance) and beta (window radius), one
+ *   pass computes
+ *     card(p)  = #{n in W(p) on the image : I[p]-alpha < I[n] < I[p]+alpha}
+ *                (Algorithm 1, the cardinality matrix; W(p) is the
+ *                (2 beta + 1)^2 window centred on p, p itself included),
+ *     and, for every p with card(p) <= 2 (Algorithm 2),
+ *     flag     = #{n in W(p) on the image : NOT (I[p]-alpha < I[n] <= I[p]+alpha)}
+ *     sum      = sum of I[n]^2 over those "open" n,
+ *     pix_count= (2 beta + 1)^2 (off-image positions included);
+ *     if flag > pix_count - 3 the pixel is replaced, in a separate output
+ *     image, by floor(sqrt(floor(sum / flag))) - the root mean square of its
+ *     open neighbourhood.  Other pixels keep their value.
+ *   Passes repeat (Section 2, iteration factor k) until a pass changes no
+ *   pixel or max_k passes that changed pixels have run.  k, the number of
+ *   passes that changed at least one pixel, is returned.  All arithmetic is
+ *   integer; results are exact (bit-identical to a direct evaluation of the
+ *   definition).
+ *
+ * Conventions
+ *   - Functions returning int return >= 0 on success and a negative HGRMS_E*
+ *     code on failure.  A failed call leaves the image unspecified only for
+ *     HGRMS_ECUDA / HGRMS_ETIMEOUT; argument errors are detected before any
+ *     device work and leave the image untouched.
+ *   - Images are dense: row r starts at img + r*cols.  No alignment is
+ *     required.  The pointer may be device memory of the handle's device
+ *     (denoised in place on the device) or host memory (pageable or pinned;
+ *     copied to the device and back inside the call).
+ *   - Calls are synchronous: when a call returns, the result is in img.
+ *     Work is issued on the handle's stream.
+ *   - A handle may be used by one host thread at a time.
+ *   - Limits: 1 <= rows, cols <= 65536; 0 <= alpha <= 255; 1 <= beta <= 7;
+ *     0 <= max_k <= 1000000.
+ */
+#ifndef HGRMS_H
+#define HGRMS_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HGRMS_OK        0
+#define HGRMS_EINVAL   (-1) /* bad argument (null pointer, size or parameter out of range) */
+#define HGRMS_ENOMEM   (-2) /* device or pinned host allocation failed */
+#define HGRMS_ECUDA    (-3) /* a CUDA runtime call or kernel failed; see hgrms_last_cuda_error */
+#define HGRMS_ETIMEOUT (-4) /* a bounded device wait gave up */
+#define HGRMS_ENODEV   (-5) /* no CUDA device, or the device index is out of range */
+
+typedef struct hgrms_ctx* hgrms_t;
+
+/* Create a handle on CUDA device `device`.  `cuda_stream` is a cudaStream_t
+ * to issue work on, or NULL for the device's default (legacy) stream.  The
+ * handle owns its device buffers (two padded image canvases and a small
+ * control block) and reuses them across calls, growing them on demand.
+ * Writes the handle to *out and returns HGRMS_OK, or a negative code (and
+ * *out = NULL). */
+int hgrms_create(hgrms_t* out, int device, void* cuda_stream);
+
+/* Release the handle and everything it owns.  NULL is accepted. */
+void hgrms_destroy(hgrms_t h);
+
+/* Denoise one image in place (the full method above).
+ * Returns k (0 <= k <= max_k) or a negative error code.  Reaching max_k is
+ * not an error; hgrms_converged() tells whether the call ended on a pass
+ * that changed nothing.  Images smaller than 2*beta+1 in either dimension
+ * are returned unchanged with k = 0 (no pixel can be replaced there). */
+int hgrms_denoise(hgrms_t h, uint8_t* img, int rows, int cols,
+                  int alpha, int beta, int max_k);
+
+/* Denoise n independent images with the same alpha, beta and max_k.
+ * imgs[i] has rows[i] x cols[i] pixels (all device pointers or all host
+ * pointers).  k_out[i] receives image i's k.  Returns HGRMS_OK or a negative
+ * code; arguments are validated for every image before any work starts. */
+int hgrms_denoise_batch(hgrms_t h, uint8_t* const* imgs, const int* rows,
+                        const int* cols, int n, int alpha, int beta, int max_k,
+                        int* k_out);
+
+/* 1 if the last hgrms_denoise ended because a pass changed no pixel (the
+ * image is a fixed point), 0 if it stopped at max_k, negative on a bad
+ * handle. */
+int hgrms_converged(hgrms_t h);
+
+/* Human-readable text for a return code (static storage). */
+const char* hgrms_strerror(int code);
+
+/* The cudaError_t of the last failing CUDA call on this handle (0 if none). */
+int hgrms_last_cuda_error(hgrms_t h);
+
+/* ---- Tuning and measurement (not part of the method) ------------------ */
+
+/* Options for hgrms_set_option. */
+#define HGRMS_OPT_KERNEL   1 /* 0 = fused multi-pass tile kernel (default), 1 = unfused one-pass kernel */
+#define HGRMS_OPT_PASSES   2 /* passes fused per launch; 0 = the built-in choice for beta */
+#define HGRMS_OPT_TIMING   3 /* 1 = time every denoising launch with CUDA events (see hgrms_stats) */
+
+/* Set an option.  Returns HGRMS_OK or HGRMS_EINVAL (unknown option or value,
+ * e.g. a pass count that has no compiled kernel for some beta is rejected at
+ * denoise time with HGRMS_EINVAL). */
+int hgrms_set_option(hgrms_t h, int option, int value);
+
+/* Statistics of the last hgrms_denoise / hgrms_denoise_batch call. */
+typedef struct hgrms_stats {
+    int    launches;        /* denoising kernel launches issued */
+    int    work_launches;   /* of those, launches that ran at least one pass */
+    int    passes;          /* passes needed: k, plus 1 if the call ended on a no-change pass */
+    int    passes_executed; /* passes the launches actually ran (a launch runs whole
+                               groups of T, so this can exceed `passes`) */
+    int    passes_per_launch; /* fused passes per launch (T) */
+    int    tile_rows;       /* core tile height of the kernel used */
+    int    tile_cols;       /* core tile width of the kernel used */
+    long long ctas_per_launch;
+    double kernel_ms;       /* HGRMS_OPT_TIMING: summed durations of the launches that ran
+                               passes (CUDA events on the handle's stream), else 0 */
+    double idle_kernel_ms;  /* HGRMS_OPT_TIMING: summed durations of the launches that found
+                               the call already finished and returned at once */
+} hgrms_stats_t;
+
+int hgrms_stats(hgrms_t h, hgrms_stats_t* out);
+
+/* The passes per launch the built-in choice uses for beta (1..7), or
+ * HGRMS_EINVAL. */
+int hgrms_default_passes(int beta);
+
+/* Whether a fused kernel with `passes` passes per launch exists for beta. */
+int hgrms_has_kernel(int beta, int passes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HGRMS_H */

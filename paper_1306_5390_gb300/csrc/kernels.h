@@ -1,0 +1,25 @@
+// Internal declarations shared by the runtime and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "common.cuh"
+
+namespace hg {
+
+struct FusedEntry;
+extern const FusedEntry kFusedB1[];
+extern const int kFusedB1Count;
+extern const FusedEntry kFusedB2[];
+extern const int kFusedB2Count;
+extern const FusedEntry kFusedB3[];
+extern const int kFusedB3Count;
+
+cudaError_t launch_plain(int beta, const PassArgs& a, cudaStream_t s);
+cudaError_t launch_ctrl_init(Ctrl* c, unsigned max_k, cudaStream_t s);
+cudaError_t launch_copy_in(const uint8_t* img, int rows, int cols, uint8_t* canvas, long long pitch,
+                           int sms, cudaStream_t s);
+cudaError_t launch_copy_out(const Ctrl* c, const uint8_t* ca, const uint8_t* cb, long long pitch,
+                            uint8_t* img, int rows, int cols, int sms, cudaStream_t s);
+
+}  // namespace hg

@@ -1,0 +1,246 @@
+"""ctypes binding of the C ABI in ``include/hgrms.h`` (argument marshalling only).
+
+Every step of the method runs in the CUDA library ``_lib/libhgrms.so``.  The
+functions below have the C names; ``denoise`` / ``denoise_batch`` are thin
+conveniences that accept numpy arrays (host memory) or CUDA torch tensors
+(device memory, denoised in place).  If the library is missing or cannot be
+loaded, every call raises ``RuntimeError``: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libhgrms.so")
+
+HGRMS_OK = 0
+HGRMS_EINVAL = -1
+HGRMS_ENOMEM = -2
+HGRMS_ECUDA = -3
+HGRMS_ETIMEOUT = -4
+HGRMS_ENODEV = -5
+
+HGRMS_OPT_KERNEL = 1
+HGRMS_OPT_PASSES = 2
+HGRMS_OPT_TIMING = 3
+
+# Every symbol the header declares (the CPU tests check the library exports them).
+EXPORTED = (
+    "hgrms_create", "hgrms_destroy", "hgrms_denoise", "hgrms_denoise_batch",
+    "hgrms_converged", "hgrms_strerror", "hgrms_last_cuda_error", "hgrms_set_option",
+    "hgrms_stats", "hgrms_default_passes", "hgrms_has_kernel",
+)
+
+
+class hgrms_stats_t(ctypes.Structure):
+    _fields_ = [
+        ("launches", ctypes.c_int),
+        ("work_launches", ctypes.c_int),
+        ("passes", ctypes.c_int),
+        ("passes_executed", ctypes.c_int),
+        ("passes_per_launch", ctypes.c_int),
+        ("tile_rows", ctypes.c_int),
+        ("tile_cols", ctypes.c_int),
+        ("ctas_per_launch", ctypes.c_longlong),
+        ("kernel_ms", ctypes.c_double),
+        ("idle_kernel_ms", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
+class HgrmsError(RuntimeError):
+    def __init__(self, code: int, what: str = ""):
+        self.code = code
+        super().__init__(f"{what}: {strerror(code)} ({code})" if what else f"{strerror(code)} ({code})")
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load_library(path: str | None = None):
+    """Load (once) and return the ctypes library; raises RuntimeError if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(
+                f"CUDA library not built: {p} is missing (run __graft_entry__.build() "
+                "or python -m paper_1306_5390_gb300.build)")
+        lib = ctypes.CDLL(p)
+        vp = ctypes.c_void_p
+        ip = ctypes.POINTER(ctypes.c_int)
+        lib.hgrms_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, vp]
+        lib.hgrms_create.restype = ctypes.c_int
+        lib.hgrms_destroy.argtypes = [vp]
+        lib.hgrms_destroy.restype = None
+        lib.hgrms_denoise.argtypes = [vp, vp] + [ctypes.c_int] * 5
+        lib.hgrms_denoise.restype = ctypes.c_int
+        lib.hgrms_denoise_batch.argtypes = [vp, ctypes.POINTER(vp), ip, ip] + [ctypes.c_int] * 4 + [ip]
+        lib.hgrms_denoise_batch.restype = ctypes.c_int
+        lib.hgrms_converged.argtypes = [vp]
+        lib.hgrms_converged.restype = ctypes.c_int
+        lib.hgrms_strerror.argtypes = [ctypes.c_int]
+        lib.hgrms_strerror.restype = ctypes.c_char_p
+        lib.hgrms_last_cuda_error.argtypes = [vp]
+        lib.hgrms_last_cuda_error.restype = ctypes.c_int
+        lib.hgrms_set_option.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+        lib.hgrms_set_option.restype = ctypes.c_int
+        lib.hgrms_stats.argtypes = [vp, ctypes.POINTER(hgrms_stats_t)]
+        lib.hgrms_stats.restype = ctypes.c_int
+        lib.hgrms_default_passes.argtypes = [ctypes.c_int]
+        lib.hgrms_default_passes.restype = ctypes.c_int
+        lib.hgrms_has_kernel.argtypes = [ctypes.c_int, ctypes.c_int]
+        lib.hgrms_has_kernel.restype = ctypes.c_int
+        _lib = lib
+        return lib
+
+
+# ---- C-named functions -----------------------------------------------------
+
+def hgrms_create(device: int = 0, cuda_stream: int | None = None) -> int:
+    h = ctypes.c_void_p()
+    rc = load_library().hgrms_create(ctypes.byref(h), int(device), cuda_stream)
+    if rc != HGRMS_OK:
+        raise HgrmsError(rc, "hgrms_create")
+    return h.value
+
+
+def hgrms_destroy(h) -> None:
+    load_library().hgrms_destroy(h)
+
+
+def hgrms_denoise(h, img_ptr: int, rows: int, cols: int, alpha: int, beta: int, max_k: int) -> int:
+    """Raw call: returns k or a negative code (not raised)."""
+    return load_library().hgrms_denoise(h, img_ptr, rows, cols, alpha, beta, max_k)
+
+
+def hgrms_denoise_batch(h, ptrs, rows, cols, alpha: int, beta: int, max_k: int, k_out) -> int:
+    n = len(ptrs)
+    P = (ctypes.c_void_p * max(n, 1))(*ptrs)
+    R = (ctypes.c_int * max(n, 1))(*rows)
+    C = (ctypes.c_int * max(n, 1))(*cols)
+    K = (ctypes.c_int * max(n, 1))()
+    rc = load_library().hgrms_denoise_batch(h, P, R, C, n, alpha, beta, max_k, K)
+    for i in range(n):
+        k_out[i] = K[i]
+    return rc
+
+
+def hgrms_converged(h) -> int:
+    return load_library().hgrms_converged(h)
+
+
+def strerror(code: int) -> str:
+    return load_library().hgrms_strerror(int(code)).decode()
+
+
+hgrms_strerror = strerror
+
+
+def hgrms_last_cuda_error(h) -> int:
+    return load_library().hgrms_last_cuda_error(h)
+
+
+def hgrms_set_option(h, option: int, value: int) -> int:
+    return load_library().hgrms_set_option(h, option, value)
+
+
+def hgrms_stats(h) -> dict:
+    st = hgrms_stats_t()
+    rc = load_library().hgrms_stats(h, ctypes.byref(st))
+    if rc != HGRMS_OK:
+        raise HgrmsError(rc, "hgrms_stats")
+    return st.as_dict()
+
+
+def hgrms_default_passes(beta: int) -> int:
+    return load_library().hgrms_default_passes(beta)
+
+
+def hgrms_has_kernel(beta: int, passes: int) -> int:
+    return load_library().hgrms_has_kernel(beta, passes)
+
+
+# ---- Conveniences --------------------------------------------------------
+
+class Denoiser:
+    """Owns one library handle (one device, one stream)."""
+
+    def __init__(self, device: int = 0, cuda_stream: int | None = None, kernel: int = 0,
+                 passes: int = 0, timing: bool = False):
+        self.h = hgrms_create(device, cuda_stream)
+        self.device = device
+        self.set_option(HGRMS_OPT_KERNEL, kernel)
+        self.set_option(HGRMS_OPT_PASSES, passes)
+        self.set_option(HGRMS_OPT_TIMING, int(bool(timing)))
+
+    def set_option(self, opt: int, value: int) -> None:
+        rc = hgrms_set_option(self.h, opt, value)
+        if rc != HGRMS_OK:
+            raise HgrmsError(rc, "hgrms_set_option")
+
+    def close(self) -> None:
+        if self.h:
+            hgrms_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @staticmethod
+    def _ptr_shape(img):
+        if isinstance(img, np.ndarray):
+            if img.dtype != np.uint8 or img.ndim != 2 or not img.flags.c_contiguous:
+                raise ValueError("image must be a C-contiguous 2-D uint8 array")
+            return img.ctypes.data, img.shape[0], img.shape[1]
+        # torch tensor (duck-typed: no import of torch here)
+        if img.dim() != 2 or not img.is_contiguous() or str(img.dtype) != "torch.uint8":
+            raise ValueError("image must be a contiguous 2-D uint8 tensor")
+        return img.data_ptr(), img.shape[0], img.shape[1]
+
+    def denoise(self, img, alpha: int, beta: int, max_k: int) -> int:
+        """Denoise ``img`` in place; returns k.  ``img``: numpy (host) or CUDA tensor."""
+        ptr, rows, cols = self._ptr_shape(img)
+        k = hgrms_denoise(self.h, ptr, rows, cols, alpha, beta, max_k)
+        if k < 0:
+            raise HgrmsError(k, "hgrms_denoise")
+        return k
+
+    def denoise_batch(self, imgs, alpha: int, beta: int, max_k: int):
+        ps = [self._ptr_shape(im) for im in imgs]
+        ks = [0] * len(ps)
+        rc = hgrms_denoise_batch(self.h, [p[0] for p in ps], [p[1] for p in ps], [p[2] for p in ps],
+                                 alpha, beta, max_k, ks)
+        if rc != HGRMS_OK:
+            raise HgrmsError(rc, "hgrms_denoise_batch")
+        return ks
+
+    def converged(self) -> bool:
+        return hgrms_converged(self.h) == 1
+
+    def stats(self) -> dict:
+        return hgrms_stats(self.h)
+
+
+def denoise(img, alpha: int, beta: int, max_k: int, device: int = 0) -> int:
+    """One-shot in-place denoise (creates and frees a handle)."""
+    with Denoiser(device) as d:
+        return d.denoise(img, alpha, beta, max_k)

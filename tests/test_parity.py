@@ -1,0 +1,223 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bit-exact comparison of every output pixel, of k and of the converged flag
+(the method is integer arithmetic, so the tolerance is zero).  Covers every
+compiled (beta, passes-per-launch) kernel, tile-straddling and ragged
+shapes, degenerate sizes, alpha edge values, max_k edge values, host and
+device pointers, the batch entry point, the 256x256 and 481x321 workloads
+in full, and the 8192x8192 workload on sampled windows checked against the
+oracle's dependency cone.
+"""
+import numpy as np
+import pytest
+
+from paper_1306_5390_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+ALL_KERNELS = [(1, 1), (1, 2), (1, 3), (1, 4), (1, 6), (1, 8), (2, 1), (2, 2), (2, 3), (2, 4),
+               (3, 1), (3, 2), (4, 1), (4, 2), (5, 1), (6, 1), (7, 1)]
+
+
+@pytest.fixture(scope="module")
+def torch_cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch
+
+
+@pytest.fixture(scope="module")
+def den(torch_cuda):
+    from paper_1306_5390_gb300 import build, hgrms
+    build.build()
+    d = hgrms.Denoiser(0)
+    yield d
+    d.close()
+
+
+def gpu_denoise(d, torch, img, alpha, beta, max_k, passes=0, kernel=0, host=False):
+    from paper_1306_5390_gb300 import hgrms
+    d.set_option(hgrms.HGRMS_OPT_PASSES, passes)
+    d.set_option(hgrms.HGRMS_OPT_KERNEL, kernel)
+    if host:
+        out = np.ascontiguousarray(img).copy()
+        k = d.denoise(out, alpha, beta, max_k)
+    else:
+        t = torch.from_numpy(np.ascontiguousarray(img).copy()).cuda()
+        k = d.denoise(t, alpha, beta, max_k)
+        out = t.cpu().numpy()
+    return out, k, d.converged()
+
+
+def assert_same(oracle_mod, d, torch, img, alpha, beta, max_k, **kw):
+    ref, k_ref, c_ref = oracle_mod.denoise(img, alpha, beta, max_k)
+    out, k, c = gpu_denoise(d, torch, img, alpha, beta, max_k, **kw)
+    bad = int((out != ref).sum())
+    assert bad == 0 and k == k_ref and c == c_ref, (
+        f"shape={img.shape} a={alpha} b={beta} max_k={max_k} {kw}: {bad} pixels differ, "
+        f"k={k} vs {k_ref}, converged={c} vs {c_ref}")
+    return k
+
+
+def test_workload_256(oracle_mod, den, torch_cuda):
+    w = synth.workload_256()
+    k = assert_same(oracle_mod, den, torch_cuda, w["noisy"], w["alpha"], w["beta"], w["max_k"])
+    assert k >= 1
+    assert_same(oracle_mod, den, torch_cuda, w["noisy"], w["alpha"], w["beta"], w["max_k"], host=True)
+
+
+@pytest.mark.parametrize("beta,passes", ALL_KERNELS)
+def test_every_kernel_on_tile_straddling_shapes(oracle_mod, den, torch_cuda, beta, passes):
+    th = 64 - 2 * (passes - 1) * beta
+    shapes = [(th + 1, 241), (2 * th - 1, 239), (th, 480), (3 * th + 5, 97)]
+    for i, (r, c) in enumerate(shapes):
+        _, noisy = synth.noisy_image(r, c, 0.3, synth.seed_for(20, 100 * beta + 10 * passes + i))
+        mk = 32 if beta <= 2 else 12
+        assert_same(oracle_mod, den, torch_cuda, noisy, 10, beta, mk, passes=passes)
+    img = synth.random_image(th + 3, 250, 5000 + beta, levels=[0, 20, 25, 30, 35, 255])
+    assert_same(oracle_mod, den, torch_cuda, img, 6, beta, 9, passes=passes)
+
+
+@pytest.mark.parametrize("beta", [1, 2, 3])
+def test_degenerate_and_ragged_shapes(oracle_mod, den, torch_cuda, beta):
+    shapes = [(1, 1), (1, 300), (300, 1), (2, 2), (2 * beta, 70), (70, 2 * beta),
+              (2 * beta + 1, 2 * beta + 1), (5, 7), (17, 255), (33, 17), (100, 1000), (481, 321)]
+    for i, (r, c) in enumerate(shapes):
+        _, noisy = synth.noisy_image(r, c, 0.25, synth.seed_for(21, 10 * beta + i))
+        assert_same(oracle_mod, den, torch_cuda, noisy, 10, beta, 32)
+        assert_same(oracle_mod, den, torch_cuda, noisy, 10, beta, 32, kernel=1)
+
+
+@pytest.mark.parametrize("alpha", [0, 1, 2, 128, 254, 255])
+def test_alpha_edges(oracle_mod, den, torch_cuda, alpha):
+    img = synth.random_image(90, 300, 900 + alpha)
+    for beta in (1, 2):
+        assert_same(oracle_mod, den, torch_cuda, img, alpha, beta, 6)
+    _, noisy = synth.noisy_image(90, 300, 0.2, synth.seed_for(22, alpha))
+    assert_same(oracle_mod, den, torch_cuda, noisy, alpha, 1, 32)
+
+
+@pytest.mark.parametrize("max_k", [0, 1, 2, 3, 4, 5, 7, 9, 33])
+def test_max_k_not_multiple_of_passes(oracle_mod, den, torch_cuda, max_k):
+    _, noisy = synth.noisy_image(200, 333, 0.5, synth.seed_for(23, max_k))
+    for passes in (1, 4, 8):
+        assert_same(oracle_mod, den, torch_cuda, noisy, 10, 1, max_k, passes=passes)
+
+
+def test_unfused_kernel_every_beta(oracle_mod, den, torch_cuda):
+    for beta in range(1, 8):
+        _, noisy = synth.noisy_image(120, 250, 0.3, synth.seed_for(24, beta))
+        assert_same(oracle_mod, den, torch_cuda, noisy, 10, beta, 10, kernel=1)
+
+
+def test_host_pointer_path(oracle_mod, den, torch_cuda):
+    for beta in (1, 2):
+        _, noisy = synth.noisy_image(333, 517, 0.3, synth.seed_for(25, beta))
+        assert_same(oracle_mod, den, torch_cuda, noisy, 10, beta, 32, host=True)
+
+
+def test_unaligned_device_pointer(oracle_mod, den, torch_cuda):
+    torch = torch_cuda
+    _, noisy = synth.noisy_image(150, 160, 0.3, synth.seed_for(26, 0))
+    ref, k_ref, c_ref = oracle_mod.denoise(noisy, 10, 1, 32)
+    buf = torch.zeros(150 * 160 + 3, dtype=torch.uint8, device="cuda")
+    view = buf[3:].view(150, 160)
+    view.copy_(torch.from_numpy(noisy))
+    k = den.denoise(view, 10, 1, 32)
+    assert k == k_ref
+    assert np.array_equal(view.cpu().numpy(), ref)
+    assert int(buf[:3].sum()) == 0
+
+
+def test_batch_matches_per_image(oracle_mod, den, torch_cuda):
+    torch = torch_cuda
+    shapes = [(128, 128), (321, 481), (481, 321), (200, 2048), (7, 9), (1, 1)]
+    imgs, refs = [], []
+    for i, (r, c) in enumerate(shapes):
+        _, noisy = synth.noisy_image(r, c, 0.05 + 0.1 * i, synth.seed_for(27, i))
+        imgs.append(torch.from_numpy(noisy).cuda())
+        refs.append(oracle_mod.denoise(noisy, 10, 1, 32))
+    ks = den.denoise_batch(imgs, 10, 1, 32)
+    for t, (ref, k_ref, _), k in zip(imgs, refs, ks):
+        assert k == k_ref
+        assert np.array_equal(t.cpu().numpy(), ref)
+    host = [synth.noisy_image(r, c, 0.2, synth.seed_for(28, i))[1] for i, (r, c) in enumerate(shapes)]
+    hrefs = [oracle_mod.denoise(h, 10, 2, 32) for h in host]
+    ks = den.denoise_batch(host, 10, 2, 32)
+    for h, (ref, k_ref, _), k in zip(host, hrefs, ks):
+        assert k == k_ref and np.array_equal(h, ref)
+
+
+def test_bsds_like_workload_subset(oracle_mod, den, torch_cuda):
+    """The 481x321 / 321x481 sweep: two images over all 30 settings, and
+    every image at one setting."""
+    seen = set()
+    for w in synth.workload_bsds_like(64):
+        i = w["image"]
+        full = i < 2
+        pick = (w["density"] == 0.30 and w["alpha"] == 10 and w["beta"] == 1)
+        if not (full or pick) or (not full and i in seen):
+            continue
+        seen.add(i)
+        assert_same(oracle_mod, den, torch_cuda, w["noisy"], w["alpha"], w["beta"], w["max_k"])
+
+
+def test_tall_and_wide_extremes(oracle_mod, den, torch_cuda):
+    for (r, c) in ((65536, 20), (12, 65536)):
+        _, noisy = synth.noisy_image(r, c, 0.3, synth.seed_for(29, r))
+        assert_same(oracle_mod, den, torch_cuda, noisy, 10, 1, 8)
+
+
+def test_argument_errors_leave_image_untouched(den, torch_cuda):
+    from paper_1306_5390_gb300 import hgrms
+    torch = torch_cuda
+    t = torch.full((10, 10), 7, dtype=torch.uint8, device="cuda")
+    for args in ((10, 10, -1, 1, 5), (10, 10, 256, 1, 5), (10, 10, 10, 0, 5), (10, 10, 10, 8, 5),
+                 (10, 10, 10, 1, -1), (0, 10, 10, 1, 5), (10, 0, 10, 1, 5), (70000, 1, 10, 1, 5)):
+        assert hgrms.hgrms_denoise(den.h, t.data_ptr(), *args) == hgrms.HGRMS_EINVAL
+    assert hgrms.hgrms_denoise(den.h, 0, 10, 10, 10, 1, 5) == hgrms.HGRMS_EINVAL
+    den.set_option(hgrms.HGRMS_OPT_PASSES, 4)
+    assert hgrms.hgrms_denoise(den.h, t.data_ptr(), 10, 10, 10, 3, 5) == hgrms.HGRMS_EINVAL
+    den.set_option(hgrms.HGRMS_OPT_PASSES, 0)
+    assert int((t != 7).sum()) == 0
+
+
+def _sampled_windows(rows, cols, win, rng):
+    pts = [(0, 0), (0, cols - win), (rows - win, 0), (rows - win, cols - win),
+           ((rows - win) // 2, (cols - win) // 2)]
+    for _ in range(3):
+        pts.append((int(rng.integers(0, rows - win)), int(rng.integers(0, cols - win))))
+    return pts
+
+
+@pytest.mark.parametrize("beta", [1, 2, 3])
+def test_8192_full_size_sampled(oracle_mod, den, torch_cuda, beta):
+    """8192x8192, 30 % impulse noise, alpha 10: the launch configuration the
+    benchmark times.  Each sampled 64x64 window is checked against the
+    oracle run for the same number of passes on a crop that contains the
+    window's dependency cone (radius = passes * beta)."""
+    torch = torch_cuda
+    w = synth.workload_8192(beta)
+    noisy = w["noisy"]
+    t = torch.from_numpy(noisy).cuda()
+    k = den.denoise(t, w["alpha"], beta, w["max_k"])
+    conv = den.converged()
+    out = t.cpu().numpy()
+    assert 0 <= k <= w["max_k"] and (conv or k == w["max_k"])
+    rows, cols = noisy.shape
+    margin = k * beta + beta
+    rng = np.random.default_rng(beta)
+    win = 64
+    for (y, x) in _sampled_windows(rows, cols, win, rng):
+        y0, x0 = max(0, y - margin), max(0, x - margin)
+        y1, x1 = min(rows, y + win + margin), min(cols, x + win + margin)
+        crop = noisy[y0:y1, x0:x1]
+        ref = crop
+        for _ in range(k):
+            ref, _ = oracle_mod.one_pass(ref, w["alpha"], beta)
+        np.testing.assert_array_equal(out[y:y + win, x:x + win], ref[y - y0:y - y0 + win, x - x0:x - x0 + win])
+    if conv:
+        # A converged result is a fixed point: one more pass changes nothing.
+        t2 = torch.from_numpy(out).cuda()
+        assert den.denoise(t2, w["alpha"], beta, 1) == 0
