@@ -19,6 +19,15 @@
 //    arithmetic and runs the exact scalar definition only for pixels with at
 //    most one closed neighbour (for alpha = 0 nothing is closed, so every
 //    interior pixel takes the exact path).
+//  * Locality of change: a pixel's output in pass t depends only on its
+//    window in the image of pass t-1.  If no pixel within beta of p changed
+//    in pass t-1, p's output in pass t equals its output in pass t-1, i.e.
+//    its current value.  With two ping-pong buffers, the buffer written by
+//    pass t already holds pass t-2's values, which equal pass t-1's at every
+//    pixel that did not change in pass t-1.  So after the first pass of a
+//    launch (which writes the whole tile), a pass only needs to recompute
+//    8-pixel row segments within beta of a segment that changed in the
+//    previous pass; all other segments are already correct in both buffers.
 //
 // Packed closed-neighbour test.  Pixel values are stored in shared memory as
 // fp16 (exact for 0..255), two pixels per 32-bit word.  For a centre value
@@ -28,6 +37,13 @@
 // argument is an odd integer), so one subtract, one fused multiply-add with
 // saturation and one add count two pixels' neighbours.  A count of 0 or 1 is
 // an fp16 bit pattern with bit 14 clear; 2 and above have it set.
+//
+// Work layout: warp w owns tile rows [R0 + 8w, R0 + 8w + 8) of every pass;
+// lane l owns the 8-pixel segment at columns [8 + 8l, 16 + 8l).  A dense pass
+// walks the 8 rows with a register ring of the 2 beta + 1 window rows; a
+// sparse pass lists the warp's active (row, segment) pairs and gives one to
+// each lane.  Candidate pixels (at most one closed neighbour) are appended to
+// a per-warp list and evaluated exactly, one per lane.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -39,22 +55,30 @@ template <int B, int T>
 struct FusedGeo {
     static constexpr int kThreads = 256;
     static constexpr int kWarps = kThreads / 32;
-    static constexpr int kRows = 8;                  // output rows per thread per pass
+    static constexpr int kRows = 8;                  // rows per warp band
     static constexpr int TW = 240;                   // core tile width (pixels)
     static constexpr int RN = kRows * kWarps;        // rows computed per pass (64)
     static constexpr int TH = RN - 2 * (T - 1) * B;  // core tile height
     static constexpr int H = T * B;                  // vertical halo
-    static constexpr int SH = TH + 2 * H;            // tile rows in shared memory
+    static constexpr int SH = TH + 2 * H;            // tile rows in shared memory (= RN + 2B)
     static constexpr int SW = TW + 2 * kPadX;        // tile columns (fp16 values)
     static constexpr int SWW = SW / 2;               // 32-bit words per tile row
-    static constexpr int R0 = H - (T - 1) * B;       // first computed row
+    static constexpr int R0 = H - (T - 1) * B;       // first computed row (= B)
     static constexpr int C0 = kPadX - 8;             // first computed column
-    static constexpr size_t kSmem = 2ull * SH * SW * sizeof(__half);
+    static constexpr int kCandCap = 512;             // per-warp candidate list capacity
+    static constexpr int kDenseAbove = 96;           // active segments (of 256) above which a band runs dense
+    // shared memory layout (bytes)
+    static constexpr size_t kBufBytes = (size_t)SH * SW * sizeof(__half);
+    static constexpr size_t kChgOff = 2 * kBufBytes;
+    static constexpr size_t kCandOff = kChgOff + 3ull * SH * sizeof(uint32_t);
+    static constexpr size_t kTaskOff = kCandOff + (size_t)kWarps * kCandCap * sizeof(uint16_t);
+    static constexpr size_t kSmem = kTaskOff + (size_t)kWarps * 256;
     // Lanes 0..31 cover columns [C0, C0 + 256): results within T*beta of
     // those edges may use wrong horizontal neighbours, so T*beta <= 8 keeps
     // the core [kPadX, kPadX + TW) exact after T passes.
     static_assert(T * B <= 8, "fused halo exceeds the computed margin");
     static_assert(TH >= 16, "tile too short");
+    static_assert(SH <= 127 && SW <= 511, "candidate encoding");
     static_assert(C0 + 8 * 32 == kPadX + TW + 8, "strip layout");
 };
 
@@ -82,21 +106,32 @@ __device__ __forceinline__ uint32_t h2_to_bytes(uint32_t a, uint32_t b) {
     return __byte_perm(ab, bb, 0x6420);
 }
 
-// One tile row as seen by one thread: fp16 pairs starting at pixel offsets
-// -B .. 6+B relative to the thread's 8-pixel strip.
+// One tile row as seen by one segment: fp16 pairs starting at pixel offsets
+// -B .. 6+B relative to the segment's first pixel.
 template <int B>
 struct Row {
-    static constexpr int WB = (B + 1) / 2;  // words needed beyond each side of the strip
+    static constexpr int WB = (B + 1) / 2;  // words needed beyond each side of the segment
     static constexpr int NP = 7 + 2 * B;
     uint32_t p[NP];
 };
 
-// Load one row: the strip's four words with one 16-byte shared load, the
-// neighbouring words from the adjacent lanes (lane 0 / lane 31 get their own
-// words, which only affects pixels outside the exact region), and the
-// odd-offset pairs by byte permutation.
 template <int B>
-__device__ __forceinline__ void load_row(const uint32_t* __restrict__ rowp, Row<B>& r) {
+__device__ __forceinline__ void make_pairs(const uint32_t (&w)[4 + 2 * Row<B>::WB], Row<B>& r) {
+    constexpr int WB = Row<B>::WB;
+#pragma unroll
+    for (int o = -B; o <= 6 + B; ++o) {
+        if ((o & 1) == 0)
+            r.p[o + B] = w[WB + o / 2];
+        else
+            r.p[o + B] = __byte_perm(w[WB + (o - 1) / 2], w[WB + (o + 1) / 2], 0x5432);
+    }
+}
+
+// Dense form: the segment's four words with one 16-byte shared load, the
+// neighbouring words from the adjacent lanes (lane 0 / lane 31 get their own
+// words, which only affects pixels outside the exact region).
+template <int B>
+__device__ __forceinline__ void load_row_shfl(const uint32_t* __restrict__ rowp, Row<B>& r) {
     constexpr int WB = Row<B>::WB;
     const uint4 c = *reinterpret_cast<const uint4*>(rowp);
     const uint32_t cw[4] = {c.x, c.y, c.z, c.w};
@@ -108,16 +143,28 @@ __device__ __forceinline__ void load_row(const uint32_t* __restrict__ rowp, Row<
         w[WB - 1 - i] = __shfl_up_sync(0xffffffffu, cw[3 - i], 1);
         w[WB + 4 + i] = __shfl_down_sync(0xffffffffu, cw[i], 1);
     }
-#pragma unroll
-    for (int o = -B; o <= 6 + B; ++o) {
-        if ((o & 1) == 0)
-            r.p[o + B] = w[WB + o / 2];
-        else
-            r.p[o + B] = __byte_perm(w[WB + (o - 1) / 2], w[WB + (o + 1) / 2], 0x5432);
-    }
+    make_pairs<B>(w, r);
 }
 
-// Add row `dy`'s closed neighbours to the counts of the strip's 8 pixels.
+// Lane-independent form (sparse passes): every word from shared memory.
+template <int B>
+__device__ __forceinline__ void load_row_lds(const uint32_t* __restrict__ rowp, Row<B>& r) {
+    constexpr int WB = Row<B>::WB;
+    const uint4 c = *reinterpret_cast<const uint4*>(rowp);
+    uint32_t w[4 + 2 * WB];
+    w[WB + 0] = c.x;
+    w[WB + 1] = c.y;
+    w[WB + 2] = c.z;
+    w[WB + 3] = c.w;
+#pragma unroll
+    for (int i = 0; i < WB; ++i) {
+        w[WB - 1 - i] = rowp[-1 - i];
+        w[WB + 4 + i] = rowp[4 + i];
+    }
+    make_pairs<B>(w, r);
+}
+
+// Add row `dy`'s closed neighbours to the counts of the segment's 8 pixels.
 template <int B>
 __device__ __forceinline__ void count_row(const Row<B>& rr, const int dy, const __half2 (&cp)[4],
                                           const __half2 two_a, __half2 (&cnt)[4]) {
@@ -134,6 +181,27 @@ __device__ __forceinline__ void count_row(const Row<B>& rr, const int dy, const 
     }
 }
 
+template <int B>
+__device__ __forceinline__ void centre_setup(const Row<B>& c, __half2 (&cp)[4], __half2 (&cnt)[4], uint4& centre) {
+    const __half2 half_ = __float2half2_rn(0.5f);
+    centre = make_uint4(c.p[B], c.p[B + 2], c.p[B + 4], c.p[B + 6]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        cp[j] = __hadd2(u2h(c.p[2 * j + B]), half_);
+        cnt[j] = __float2half2_rn(0.f);
+    }
+}
+
+// 8-bit mask of the segment's pixels with at most one closed neighbour
+// (count bit 14 clear).
+__device__ __forceinline__ uint32_t candidate_mask(const __half2 (&cnt)[4]) {
+    const uint32_t a = __byte_perm(h2u(cnt[0]), h2u(cnt[1]), 0x7531);  // high bytes
+    const uint32_t b = __byte_perm(h2u(cnt[2]), h2u(cnt[3]), 0x7531);
+    const uint32_t ma = ((~a >> 6) & 0x01010101u) * 0x01020408u >> 24;  // pixel i -> bit i
+    const uint32_t mb = ((~b >> 6) & 0x01010101u) * 0x01020408u >> 24;
+    return (ma & 0xFu) | ((mb & 0xFu) << 4);
+}
+
 // Exact Algorithm 2 for one interior pixel at tile position (y, x): returns
 // the replacement value, or -1 when the pixel is not replaced.  Values are
 // integers below 2^24, so float arithmetic is exact; floor(sum / flag) is
@@ -141,7 +209,7 @@ __device__ __forceinline__ void count_row(const Row<B>& rr, const int dy, const 
 // integer, far above float rounding at these magnitudes, and the square
 // root is correctly rounded (floor of it is exact for arguments <= 65025).
 template <int B, int SW>
-__device__ __noinline__ int exact_replacement(const __half* __restrict__ in, int y, int x, int alpha) {
+__device__ __forceinline__ int exact_replacement(const __half* __restrict__ in, int y, int x, int alpha) {
     const float ip = __half2float(in[y * SW + x]);
     const float hi = ip + (float)alpha + 1.f;
     const float lo = ip - (float)alpha;
@@ -152,10 +220,9 @@ __device__ __noinline__ int exact_replacement(const __half* __restrict__ in, int
 #pragma unroll
         for (int dx = -B; dx <= B; ++dx) {
             const float v = __half2float(in[(y + dy) * SW + x + dx]);
-            if (!(v < hi && v > lo)) {
-                sum = fmaf(v, v, sum);
-                ++flag;
-            }
+            const bool open = !(v < hi && v > lo);
+            sum += open ? v * v : 0.f;
+            flag += open ? 1 : 0;
         }
     constexpr int kPixCount = (2 * B + 1) * (2 * B + 1);
     if (flag > kPixCount - 3) {
@@ -165,22 +232,78 @@ __device__ __noinline__ int exact_replacement(const __half* __restrict__ in, int
     return -1;
 }
 
-// One pass over this thread's strip: 8 columns x 8 rows starting at tile row
-// ys and word ws.  Writes the strip to `out`; returns whether a core pixel
-// changed.
+// Per-pass context shared by the helpers below.
 template <int B, int T>
-__device__ __forceinline__ bool pass_strip(const uint32_t* __restrict__ in, uint32_t* __restrict__ out,
-                                           const int ys, const int ws, const __half2 two_a,
-                                           const int x0, const int y0, const int rows, const int cols,
-                                           const int alpha) {
+struct PassCtx {
+    using G = FusedGeo<B, T>;
+    const uint32_t* in;
+    uint32_t* out;
+    uint32_t* chg_cur;   // change map written by this pass (bit l of row y: segment l changed)
+    uint16_t* cand;      // this warp's candidate list
+    int ncand;           // entries in the list (warp-uniform)
+    int x0, y0, rows, cols, alpha;
+    bool changed_core;   // this lane saw a core pixel change
+};
+
+// Evaluate and clear the warp's candidate list.
+template <int B, int T>
+__device__ __forceinline__ void flush_candidates(PassCtx<B, T>& c, const int lane) {
+    using G = FusedGeo<B, T>;
+    __syncwarp();
+    const __half* hin = reinterpret_cast<const __half*>(c.in);
+    __half* hout = reinterpret_cast<__half*>(c.out);
+    for (int i = lane; i < c.ncand; i += 32) {
+        const uint32_t e = c.cand[i];
+        const int y = (int)(e >> 9), x = (int)(e & 511u);
+        const int gx = c.x0 + x - kPadX, gy = c.y0 + y - G::H;
+        if (gy < B || gy >= c.rows - B || gx < B || gx >= c.cols - B) continue;
+        const int v = exact_replacement<B, G::SW>(hin, y, x, c.alpha);
+        if (v < 0) continue;
+        const __half hv = __int2half_rn(v);
+        if (__half_as_ushort(hv) == __half_as_ushort(hin[y * G::SW + x])) continue;
+        hout[y * G::SW + x] = hv;
+        atomicOr(&c.chg_cur[y], 1u << ((x - G::C0) >> 3));
+        if (y >= G::H && y < G::H + G::TH && x >= kPadX && x < kPadX + G::TW) c.changed_core = true;
+    }
+    __syncwarp();
+    c.ncand = 0;
+}
+
+// Append this lane's candidates (mask over the 8 pixels of the segment at
+// tile row y, first column x) to the warp's list.  Warp-collective.
+template <int B, int T>
+__device__ __forceinline__ void append_candidates(PassCtx<B, T>& c, const int lane, uint32_t mask, const int y,
+                                                  const int x) {
+    using G = FusedGeo<B, T>;
+    const int n = __popc(mask);
+    int incl = n;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    if (c.ncand + total > G::kCandCap) flush_candidates<B, T>(c, lane);
+    int off = c.ncand + incl - n;
+    const uint32_t base = ((uint32_t)y << 9) | (uint32_t)x;
+    while (mask) {
+        const int b = __ffs(mask) - 1;
+        c.cand[off++] = (uint16_t)(base + b);
+        mask &= mask - 1;
+    }
+    c.ncand += total;
+}
+
+// Dense pass over the warp's 8-row band.
+template <int B, int T>
+__device__ __forceinline__ void band_dense(PassCtx<B, T>& c, const int ys, const int ws, const int lane,
+                                           const __half2 two_a) {
     using G = FusedGeo<B, T>;
     constexpr bool kRing = (B <= 2);
-    const __half2 half_ = __float2half2_rn(0.5f);
-    bool changed = false;
     Row<B> win[kRing ? 2 * B + 1 : 1];
     if constexpr (kRing) {
 #pragma unroll
-        for (int d = 0; d < 2 * B; ++d) load_row<B>(in + (ys - B + d) * G::SWW + ws, win[d + 1]);
+        for (int d = 0; d < 2 * B; ++d) load_row_shfl<B>(c.in + (ys - B + d) * G::SWW + ws, win[d + 1]);
     }
 #pragma unroll
     for (int r = 0; r < G::kRows; ++r) {
@@ -190,67 +313,99 @@ __device__ __forceinline__ bool pass_strip(const uint32_t* __restrict__ in, uint
         if constexpr (kRing) {
 #pragma unroll
             for (int d = 0; d < 2 * B; ++d) win[d] = win[d + 1];
-            load_row<B>(in + (y + B) * G::SWW + ws, win[2 * B]);
-            const Row<B>& c = win[B];
-            centre = make_uint4(c.p[B], c.p[B + 2], c.p[B + 4], c.p[B + 6]);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                cp[j] = __hadd2(u2h(c.p[2 * j + B]), half_);
-                cnt[j] = __float2half2_rn(0.f);
-            }
+            load_row_shfl<B>(c.in + (y + B) * G::SWW + ws, win[2 * B]);
+            centre_setup<B>(win[B], cp, cnt, centre);
 #pragma unroll
             for (int dy = -B; dy <= B; ++dy) count_row<B>(win[dy + B], dy, cp, two_a, cnt);
         } else {
             Row<B>& rr = win[0];
-            load_row<B>(in + y * G::SWW + ws, rr);
-            centre = make_uint4(rr.p[B], rr.p[B + 2], rr.p[B + 4], rr.p[B + 6]);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                cp[j] = __hadd2(u2h(rr.p[2 * j + B]), half_);
-                cnt[j] = __float2half2_rn(0.f);
-            }
+            load_row_shfl<B>(c.in + y * G::SWW + ws, rr);
+            centre_setup<B>(rr, cp, cnt, centre);
             count_row<B>(rr, 0, cp, two_a, cnt);
 #pragma unroll
             for (int dy = -B; dy <= B; ++dy) {
                 if (dy == 0) continue;
-                load_row<B>(in + (y + dy) * G::SWW + ws, rr);
+                load_row_shfl<B>(c.in + (y + dy) * G::SWW + ws, rr);
                 count_row<B>(rr, dy, cp, two_a, cnt);
             }
         }
-        *reinterpret_cast<uint4*>(out + y * G::SWW + ws) = centre;
+        *reinterpret_cast<uint4*>(c.out + y * G::SWW + ws) = centre;
         const uint32_t all = h2u(cnt[0]) & h2u(cnt[1]) & h2u(cnt[2]) & h2u(cnt[3]);
-        if ((all & 0x40004000u) != 0x40004000u) {
-            const __half* hin = reinterpret_cast<const __half*>(in);
-            __half* hout = reinterpret_cast<__half*>(out);
-            const int gy = y0 + y - G::H;
-            const bool row_interior = gy >= B && gy < rows - B;
-            const bool row_core = y >= G::H && y < G::H + G::TH;
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-#pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    if ((h2u(cnt[j]) >> (16 * hh)) & 0x4000u) continue;
-                    const int x = 2 * ws + 2 * j + hh;
-                    const int gx = x0 + x - kPadX;
-                    if (!row_interior || gx < B || gx >= cols - B) continue;
-                    const int v = exact_replacement<B, G::SW>(hin, y, x, alpha);
-                    if (v < 0) continue;
-                    const __half hv = __int2half_rn(v);
-                    hout[y * G::SW + x] = hv;
-                    if (row_core && x >= kPadX && x < kPadX + G::TW &&
-                        __half_as_ushort(hv) != __half_as_ushort(hin[y * G::SW + x]))
-                        changed = true;
-                }
+        const bool has = (all & 0x40004000u) != 0x40004000u;
+        if (__any_sync(0xffffffffu, has)) {
+            const uint32_t m = has ? candidate_mask(cnt) : 0u;
+            append_candidates<B, T>(c, lane, m, y, 2 * ws);
         }
     }
-    return changed;
+}
+
+// One (row, segment) of a sparse pass, computed by one lane.
+template <int B, int T>
+__device__ __forceinline__ uint32_t segment_lds(PassCtx<B, T>& c, const int y, const int ws, const __half2 two_a) {
+    using G = FusedGeo<B, T>;
+    Row<B> rr;
+    __half2 cp[4], cnt[4];
+    uint4 centre;
+    load_row_lds<B>(c.in + y * G::SWW + ws, rr);
+    centre_setup<B>(rr, cp, cnt, centre);
+    count_row<B>(rr, 0, cp, two_a, cnt);
+#pragma unroll
+    for (int dy = -B; dy <= B; ++dy) {
+        if (dy == 0) continue;
+        load_row_lds<B>(c.in + (y + dy) * G::SWW + ws, rr);
+        count_row<B>(rr, dy, cp, two_a, cnt);
+    }
+    *reinterpret_cast<uint4*>(c.out + y * G::SWW + ws) = centre;
+    const uint32_t all = h2u(cnt[0]) & h2u(cnt[1]) & h2u(cnt[2]) & h2u(cnt[3]);
+    return ((all & 0x40004000u) != 0x40004000u) ? candidate_mask(cnt) : 0u;
+}
+
+// Sparse pass over the warp's band: only segments within beta rows / one
+// segment of a segment that changed in the previous pass.  `act` (lanes
+// 0..7) is the active mask of band row `lane`.
+template <int B, int T>
+__device__ __forceinline__ void band_sparse(PassCtx<B, T>& c, uint8_t* tasks, const int ys, const int lane,
+                                            const uint32_t act, const __half2 two_a) {
+    // list the active (row, segment) pairs
+    const int n = lane < 8 ? __popc(act) : 0;
+    int incl = n;
+#pragma unroll
+    for (int d = 1; d < 8; d <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 7);
+    if (lane < 8) {
+        int off = incl - n;
+        uint32_t m = act;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            tasks[off++] = (uint8_t)((lane << 5) | b);
+            m &= m - 1;
+        }
+    }
+    __syncwarp();
+    for (int base = 0; base < total; base += 32) {
+        const int i = base + lane;
+        uint32_t mask = 0;
+        int y = 0, x = 0;
+        if (i < total) {
+            const int t = tasks[i];
+            y = ys + (t >> 5);
+            const int seg = t & 31;
+            const int ws = FusedGeo<B, T>::C0 / 2 + 4 * seg;
+            x = 2 * ws;
+            mask = segment_lds<B, T>(c, y, ws, two_a);
+        }
+        if (__any_sync(0xffffffffu, mask != 0u)) append_candidates<B, T>(c, lane, mask, y, x);
+    }
 }
 
 template <int B, int T>
-__global__ void __launch_bounds__(256, (B == 1 ? 3 : 2))
+__global__ void __launch_bounds__(256, 2)
 fused_kernel(PassArgs a) {
     using G = FusedGeo<B, T>;
-    extern __shared__ __align__(16) uint32_t smem[];
+    extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int s_np;
     __shared__ unsigned s_cur;
     const int tid = threadIdx.x;
@@ -267,8 +422,11 @@ fused_kernel(PassArgs a) {
     const int tx = blockIdx.x % a.tiles_x;
     const int ty = blockIdx.x / a.tiles_x;
     const int x0 = tx * G::TW, y0 = ty * G::TH;
-    uint32_t* buf0 = smem;
-    uint32_t* buf1 = smem + G::SH * G::SWW;
+    uint32_t* buf0 = reinterpret_cast<uint32_t*>(smem);
+    uint32_t* buf1 = reinterpret_cast<uint32_t*>(smem + G::kBufBytes);
+    uint32_t* chg = reinterpret_cast<uint32_t*>(smem + G::kChgOff);  // 3 maps of SH rows
+    uint16_t* cand = reinterpret_cast<uint16_t*>(smem + G::kCandOff) + warp * G::kCandCap;
+    uint8_t* tasks = smem + G::kTaskOff + warp * 256;
 
     // Tile with halo: image rows [y0 - H, y0 + TH + H), columns [x0 - 16,
     // x0 + TW + 16); always inside the canvas.  Bytes -> fp16 pairs.
@@ -287,6 +445,7 @@ fused_kernel(PassArgs a) {
             d[0] = lo;
             d[1] = hi;
         }
+        for (int i = tid; i < G::SH; i += G::kThreads) chg[i] = 0u;  // map written by pass 0
     }
     __syncthreads();
 
@@ -294,11 +453,45 @@ fused_kernel(PassArgs a) {
     const __half2 two_a = __float2half2_rn(2.f * (float)a.alpha);
     const int ys = G::R0 + warp * G::kRows;
     const int ws = G::C0 / 2 + 4 * lane;
+    PassCtx<B, T> c;
+    c.cand = cand;
+    c.ncand = 0;
+    c.x0 = x0;
+    c.y0 = y0;
+    c.rows = a.rows;
+    c.cols = a.cols;
+    c.alpha = a.alpha;
     for (int t = 0; t < np; ++t) {
-        const uint32_t* in = (t & 1) ? buf1 : buf0;
-        uint32_t* out = (t & 1) ? buf0 : buf1;
-        const bool ch = pass_strip<B, T>(in, out, ys, ws, two_a, x0, y0, a.rows, a.cols, a.alpha);
-        if (__syncthreads_or(ch)) cta_mask |= 1u << t;
+        c.in = (t & 1) ? buf1 : buf0;
+        c.out = (t & 1) ? buf0 : buf1;
+        c.chg_cur = chg + (t % 3) * G::SH;
+        const uint32_t* chg_prev = chg + ((t + 2) % 3) * G::SH;
+        uint32_t* chg_next = chg + ((t + 1) % 3) * G::SH;  // read last in pass t-1; cleared for pass t+1
+        for (int i = tid; i < G::SH; i += G::kThreads) chg_next[i] = 0u;
+        c.changed_core = false;
+        bool dense = (t == 0);
+        uint32_t act = 0;
+        if (!dense) {
+            if (lane < 8) {
+                const int y = ys + lane;
+#pragma unroll
+                for (int dy = -B; dy <= B; ++dy) {
+                    const uint32_t m = chg_prev[y + dy];
+                    act |= m | (m << 1) | (m >> 1);
+                }
+            }
+            int na = lane < 8 ? __popc(act) : 0;
+#pragma unroll
+            for (int d = 4; d >= 1; d >>= 1) na += __shfl_xor_sync(0xffffffffu, na, d);
+            na = __shfl_sync(0xffffffffu, na, 0);
+            dense = na > G::kDenseAbove;
+        }
+        if (dense)
+            band_dense<B, T>(c, ys, ws, lane, two_a);
+        else
+            band_sparse<B, T>(c, tasks, ys, lane, act, two_a);
+        flush_candidates<B, T>(c, lane);
+        if (__syncthreads_or(c.changed_core)) cta_mask |= 1u << t;
     }
     const uint32_t* fin = (np & 1) ? buf1 : buf0;
 
@@ -307,15 +500,15 @@ fused_kernel(PassArgs a) {
         uint8_t* base = dst + (long long)(kPadY + y0) * a.pitch + kPadX + x0;
         constexpr int CH = G::TW / 16;
         for (int i = tid; i < G::TH * CH; i += G::kThreads) {
-            const int r = i / CH, c = i - r * CH;
-            const uint4* s = reinterpret_cast<const uint4*>(fin + (G::H + r) * G::SWW + kPadX / 2 + c * 8);
+            const int r = i / CH, cc = i - r * CH;
+            const uint4* s = reinterpret_cast<const uint4*>(fin + (G::H + r) * G::SWW + kPadX / 2 + cc * 8);
             const uint4 p = s[0], q = s[1];
             uint4 o;
             o.x = h2_to_bytes(p.x, p.y);
             o.y = h2_to_bytes(p.z, p.w);
             o.z = h2_to_bytes(q.x, q.y);
             o.w = h2_to_bytes(q.z, q.w);
-            *reinterpret_cast<uint4*>(base + (long long)r * a.pitch + c * 16) = o;
+            *reinterpret_cast<uint4*>(base + (long long)r * a.pitch + cc * 16) = o;
         }
     }
     if (tid == 0) finish_launch(a.ctrl, cta_mask, np, gridDim.x);

@@ -51,8 +51,8 @@ const hg::FusedEntry* find_fused(int beta, int T) {
 
 int default_passes(int beta) {
     switch (beta) {
-        case 1: return 4;
-        case 2: return 2;
+        case 1: return 8;
+        case 2: return 4;
         case 3: return 2;
         case 4: return 2;
         default: return 1;
