@@ -38,12 +38,13 @@
 // saturation and one add count two pixels' neighbours.  A count of 0 or 1 is
 // an fp16 bit pattern with bit 14 clear; 2 and above have it set.
 //
-// Work layout: warp w owns tile rows [R0 + 8w, R0 + 8w + 8) of every pass;
-// lane l owns the 8-pixel segment at columns [8 + 8l, 16 + 8l).  A dense pass
-// walks the 8 rows with a register ring of the 2 beta + 1 window rows; a
-// sparse pass lists the warp's active (row, segment) pairs and gives one to
-// each lane.  Candidate pixels (at most one closed neighbour) are appended to
-// a per-warp list and evaluated exactly, one per lane.
+// Work layout: a pass computes rows [R0, R0 + 64) and 32 segments of 8
+// pixels per row (columns [8, 264)).  In a dense pass warp w walks rows
+// [R0 + 8w, R0 + 8w + 8) with a register ring of the 2 beta + 1 window rows,
+// lane l owning segment l.  A sparse pass builds a CTA-wide list of the
+// active (row, segment) pairs and every lane of every warp takes one.
+// Candidate pixels (at most one closed neighbour) are appended to a per-warp
+// list and evaluated exactly, one per lane.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -65,14 +66,18 @@ struct FusedGeo {
     static constexpr int SWW = SW / 2;               // 32-bit words per tile row
     static constexpr int R0 = H - (T - 1) * B;       // first computed row (= B)
     static constexpr int C0 = kPadX - 8;             // first computed column
-    static constexpr int kCandCap = 512;             // per-warp candidate list capacity
-    static constexpr int kDenseAbove = 96;           // active segments (of 256) above which a band runs dense
+    static constexpr int kSegs = 32 * RN;            // 8-pixel row segments computed per pass
+    static constexpr int kSegsPerCore = TW / 8;      // core segments per row (30)
+    static constexpr int kCandCap = 8 * 256;         // per-warp candidate list: a whole band
+    static constexpr int kDenseAbove = kSegs * 3 / 8;  // active segments above which a pass runs dense
+    static constexpr int kDenseChanges = 96;         // changed pixels in pass t-1 above which pass t runs dense
     // shared memory layout (bytes)
     static constexpr size_t kBufBytes = (size_t)SH * SW * sizeof(__half);
     static constexpr size_t kChgOff = 2 * kBufBytes;
     static constexpr size_t kCandOff = kChgOff + 3ull * SH * sizeof(uint32_t);
     static constexpr size_t kTaskOff = kCandOff + (size_t)kWarps * kCandCap * sizeof(uint16_t);
-    static constexpr size_t kSmem = kTaskOff + (size_t)kWarps * 256;
+    static constexpr size_t kCntOff = kTaskOff + (size_t)kWarps * 256;
+    static constexpr size_t kSmem = kCntOff + 4 * sizeof(int);
     // Lanes 0..31 cover columns [C0, C0 + 256): results within T*beta of
     // those edges may use wrong horizontal neighbours, so T*beta <= 8 keeps
     // the core [kPadX, kPadX + TW) exact after T passes.
@@ -242,6 +247,8 @@ struct PassCtx {
     uint16_t* cand;      // this warp's candidate list
     int ncand;           // entries in the list (warp-uniform)
     int x0, y0, rows, cols, alpha;
+    int* nchanged;       // shared counters of changed pixels per pass (3, rotating)
+    int cnt_idx;         // counter of this pass
     bool changed_core;   // this lane saw a core pixel change
 };
 
@@ -252,6 +259,7 @@ __device__ __forceinline__ void flush_candidates(PassCtx<B, T>& c, const int lan
     __syncwarp();
     const __half* hin = reinterpret_cast<const __half*>(c.in);
     __half* hout = reinterpret_cast<__half*>(c.out);
+    int nch = 0;
     for (int i = lane; i < c.ncand; i += 32) {
         const uint32_t e = c.cand[i];
         const int y = (int)(e >> 9), x = (int)(e & 511u);
@@ -263,44 +271,37 @@ __device__ __forceinline__ void flush_candidates(PassCtx<B, T>& c, const int lan
         if (__half_as_ushort(hv) == __half_as_ushort(hin[y * G::SW + x])) continue;
         hout[y * G::SW + x] = hv;
         atomicOr(&c.chg_cur[y], 1u << ((x - G::C0) >> 3));
+        ++nch;
         if (y >= G::H && y < G::H + G::TH && x >= kPadX && x < kPadX + G::TW) c.changed_core = true;
     }
+    nch = __reduce_add_sync(0xffffffffu, nch);
+    if (lane == 0 && nch) atomicAdd(&c.nchanged[c.cnt_idx], nch);
     __syncwarp();
     c.ncand = 0;
 }
 
-// Append this lane's candidates (mask over the 8 pixels of the segment at
-// tile row y, first column x) to the warp's list.  Warp-collective.
-template <int B, int T>
-__device__ __forceinline__ void append_candidates(PassCtx<B, T>& c, const int lane, uint32_t mask, const int y,
-                                                  const int x) {
-    using G = FusedGeo<B, T>;
-    const int n = __popc(mask);
+// Warp-wide exclusive prefix sum of n; *total receives the sum.
+__device__ __forceinline__ int warp_excl_scan(const int lane, const int n, int* total) {
     int incl = n;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
         const int v = __shfl_up_sync(0xffffffffu, incl, d);
         if (lane >= d) incl += v;
     }
-    const int total = __shfl_sync(0xffffffffu, incl, 31);
-    if (c.ncand + total > G::kCandCap) flush_candidates<B, T>(c, lane);
-    int off = c.ncand + incl - n;
-    const uint32_t base = ((uint32_t)y << 9) | (uint32_t)x;
-    while (mask) {
-        const int b = __ffs(mask) - 1;
-        c.cand[off++] = (uint16_t)(base + b);
-        mask &= mask - 1;
-    }
-    c.ncand += total;
+    *total = __shfl_sync(0xffffffffu, incl, 31);
+    return incl - n;
 }
 
-// Dense pass over the warp's 8-row band.
+// Dense pass over the warp's 8-row band.  Candidate bits of the band are
+// gathered in one 64-bit mask per lane (bit 8r + i: row r, pixel i of the
+// lane's segment) and appended to the (empty) warp list in one step.
 template <int B, int T>
 __device__ __forceinline__ void band_dense(PassCtx<B, T>& c, const int ys, const int ws, const int lane,
                                            const __half2 two_a) {
     using G = FusedGeo<B, T>;
     constexpr bool kRing = (B <= 2);
     Row<B> win[kRing ? 2 * B + 1 : 1];
+    unsigned long long m64 = 0ull;
     if constexpr (kRing) {
 #pragma unroll
         for (int d = 0; d < 2 * B; ++d) load_row_shfl<B>(c.in + (ys - B + d) * G::SWW + ws, win[d + 1]);
@@ -331,11 +332,19 @@ __device__ __forceinline__ void band_dense(PassCtx<B, T>& c, const int ys, const
         }
         *reinterpret_cast<uint4*>(c.out + y * G::SWW + ws) = centre;
         const uint32_t all = h2u(cnt[0]) & h2u(cnt[1]) & h2u(cnt[2]) & h2u(cnt[3]);
-        const bool has = (all & 0x40004000u) != 0x40004000u;
-        if (__any_sync(0xffffffffu, has)) {
-            const uint32_t m = has ? candidate_mask(cnt) : 0u;
-            append_candidates<B, T>(c, lane, m, y, 2 * ws);
+        if ((all & 0x40004000u) != 0x40004000u)
+            m64 |= (unsigned long long)candidate_mask(cnt) << (8 * r);
+    }
+    if (__any_sync(0xffffffffu, m64 != 0ull)) {
+        int total;
+        int off = warp_excl_scan(lane, __popcll(m64), &total);
+        const uint32_t x = (uint32_t)(2 * ws);
+        while (m64) {
+            const int b = __ffsll((long long)m64) - 1;
+            c.cand[off++] = (uint16_t)((((uint32_t)(ys + (b >> 3))) << 9) | (x + (uint32_t)(b & 7)));
+            m64 &= m64 - 1ull;
         }
+        c.ncand = total;
     }
 }
 
@@ -360,14 +369,25 @@ __device__ __forceinline__ uint32_t segment_lds(PassCtx<B, T>& c, const int y, c
     return ((all & 0x40004000u) != 0x40004000u) ? candidate_mask(cnt) : 0u;
 }
 
-// Sparse pass over the warp's band: only segments within beta rows / one
-// segment of a segment that changed in the previous pass.  `act` (lanes
-// 0..7) is the active mask of band row `lane`.
+// Sparse pass: warp w takes the active segments of its interleaved rows
+// R0 + w + 8r (r = 0..7), one segment per lane.  A segment is active when a
+// segment within beta rows and one segment sideways changed in the previous
+// pass (`predilated`: the map already includes the sideways neighbours).
 template <int B, int T>
-__device__ __forceinline__ void band_sparse(PassCtx<B, T>& c, uint8_t* tasks, const int ys, const int lane,
-                                            const uint32_t act, const __half2 two_a) {
-    // list the active (row, segment) pairs
-    const int n = lane < 8 ? __popc(act) : 0;
+__device__ __forceinline__ void warp_sparse(PassCtx<B, T>& c, uint8_t* tasks, const uint32_t* chg_prev,
+                                            const bool predilated, const int warp, const int lane,
+                                            const __half2 two_a) {
+    using G = FusedGeo<B, T>;
+    uint32_t act = 0;
+    if (lane < 8) {
+        const int y = G::R0 + warp + 8 * lane;
+#pragma unroll
+        for (int dy = -B; dy <= B; ++dy) {
+            const uint32_t m = chg_prev[y + dy];
+            act |= predilated ? m : (m | (m << 1) | (m >> 1));
+        }
+    }
+    const int n = __popc(act);
     int incl = n;
 #pragma unroll
     for (int d = 1; d < 8; d <<= 1) {
@@ -391,14 +411,36 @@ __device__ __forceinline__ void band_sparse(PassCtx<B, T>& c, uint8_t* tasks, co
         int y = 0, x = 0;
         if (i < total) {
             const int t = tasks[i];
-            y = ys + (t >> 5);
-            const int seg = t & 31;
-            const int ws = FusedGeo<B, T>::C0 / 2 + 4 * seg;
+            y = G::R0 + warp + 8 * (t >> 5);
+            const int ws = G::C0 / 2 + 4 * (t & 31);
             x = 2 * ws;
             mask = segment_lds<B, T>(c, y, ws, two_a);
         }
-        if (__any_sync(0xffffffffu, mask != 0u)) append_candidates<B, T>(c, lane, mask, y, x);
+        if (__any_sync(0xffffffffu, mask != 0u)) {
+            if (c.ncand + 32 * 8 > G::kCandCap) flush_candidates<B, T>(c, lane);
+            int tot;
+            int off = c.ncand + warp_excl_scan(lane, __popc(mask), &tot);
+            const uint32_t base_e = ((uint32_t)y << 9) | (uint32_t)x;
+            while (mask) {
+                const int b = __ffs(mask) - 1;
+                c.cand[off++] = (uint16_t)(base_e + (uint32_t)b);
+                mask &= mask - 1;
+            }
+            c.ncand += tot;
+        }
     }
+}
+
+// Bits [start, start + 64) of a row of the segment change map (positions
+// outside [0, 32 * nwords) read as 0; start may be negative).
+__device__ __forceinline__ unsigned long long map_bits(const uint32_t* __restrict__ row, int nwords, int start) {
+    const int w0 = start >= 0 ? (start >> 5) : -((31 - start) >> 5);
+    const int sh = start - 32 * w0;
+    const uint32_t a = (w0 >= 0 && w0 < nwords) ? __ldcg(row + w0) : 0u;
+    const uint32_t b = (w0 + 1 >= 0 && w0 + 1 < nwords) ? __ldcg(row + w0 + 1) : 0u;
+    const uint32_t c = (w0 + 2 >= 0 && w0 + 2 < nwords) ? __ldcg(row + w0 + 2) : 0u;
+    const unsigned long long lo = ((unsigned long long)b << 32) | a;
+    return sh ? ((lo >> sh) | ((unsigned long long)c << (64 - sh))) : lo;
 }
 
 template <int B, int T>
@@ -407,16 +449,18 @@ fused_kernel(PassArgs a) {
     using G = FusedGeo<B, T>;
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int s_np;
-    __shared__ unsigned s_cur;
+    __shared__ unsigned s_cur, s_launch;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
         s_np = launch_passes(a.ctrl, T);
         s_cur = __ldcg(&a.ctrl->cur);
+        s_launch = __ldcg(&a.ctrl->work_launches);
     }
     __syncthreads();
     const int np = s_np;
     if (np == 0) return;
+    const unsigned L = s_launch;
     const uint8_t* src = s_cur ? a.canvas_b : a.canvas_a;
     uint8_t* dst = s_cur ? const_cast<uint8_t*>(a.canvas_a) : a.canvas_b;
     const int tx = blockIdx.x % a.tiles_x;
@@ -427,25 +471,55 @@ fused_kernel(PassArgs a) {
     uint32_t* chg = reinterpret_cast<uint32_t*>(smem + G::kChgOff);  // 3 maps of SH rows
     uint16_t* cand = reinterpret_cast<uint16_t*>(smem + G::kCandOff) + warp * G::kCandCap;
     uint8_t* tasks = smem + G::kTaskOff + warp * 256;
+    int* s_cnt = reinterpret_cast<int*>(smem + G::kCntOff);  // [0..2]: changed pixels per pass; [3]: pass-0 activity
+    const size_t map_size = (size_t)a.rows * (size_t)a.map_words;
+    uint32_t* map_out = a.seg_maps + (size_t)(L % 3u) * map_size;
+    const uint32_t* map_in = a.seg_maps + (size_t)((L + 2u) % 3u) * map_size;
+    uint32_t* map_clr = a.seg_maps + (size_t)((L + 1u) % 3u) * map_size;
+    const int gseg0 = x0 / 8 - 1;  // global segment of tile segment 0
 
     // Tile with halo: image rows [y0 - H, y0 + TH + H), columns [x0 - 16,
-    // x0 + TW + 16); always inside the canvas.  Bytes -> fp16 pairs.
+    // x0 + TW + 16); always inside the canvas.  Bytes -> fp16 pairs, into
+    // both buffers (so that a sparse first pass finds every segment it does
+    // not recompute already in its output buffer).
     {
         const uint8_t* base = src + (long long)(kPadY + y0 - G::H) * a.pitch + x0;
         constexpr int CH = G::SW / 16;
         for (int i = tid; i < G::SH * CH; i += G::kThreads) {
-            const int r = i / CH, c = i - r * CH;
-            const uint4 v = __ldg(reinterpret_cast<const uint4*>(base + (long long)r * a.pitch + c * 16));
+            const int r = i / CH, cc = i - r * CH;
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(base + (long long)r * a.pitch + cc * 16));
             uint4 lo, hi;
             lo.x = bytes_to_h2(v.x, 0x4140u); lo.y = bytes_to_h2(v.x, 0x4342u);
             lo.z = bytes_to_h2(v.y, 0x4140u); lo.w = bytes_to_h2(v.y, 0x4342u);
             hi.x = bytes_to_h2(v.z, 0x4140u); hi.y = bytes_to_h2(v.z, 0x4342u);
             hi.z = bytes_to_h2(v.w, 0x4140u); hi.w = bytes_to_h2(v.w, 0x4342u);
-            uint4* d = reinterpret_cast<uint4*>(buf0 + r * G::SWW + c * 8);
-            d[0] = lo;
-            d[1] = hi;
+            uint4* d0 = reinterpret_cast<uint4*>(buf0 + r * G::SWW + cc * 8);
+            uint4* d1 = reinterpret_cast<uint4*>(buf1 + r * G::SWW + cc * 8);
+            d0[0] = lo;
+            d0[1] = hi;
+            d1[0] = lo;
+            d1[1] = hi;
         }
-        for (int i = tid; i < G::SH; i += G::kThreads) chg[i] = 0u;  // map written by pass 0
+        if (tid < 4) s_cnt[tid] = 0;
+        // Pass 0 reads map 2: the previous launch's last-pass changes, each
+        // segment widened by one segment to both sides.
+        int act0 = 0;
+        for (int y = tid; y < G::SH; y += G::kThreads) {
+            chg[y] = 0u;  // written by pass 0
+            uint32_t d = 0u;
+            const int gy = y0 - G::H + y;
+            if (L > 0 && gy >= 0 && gy < a.rows) {
+                const unsigned long long bits = map_bits(map_in + (size_t)gy * a.map_words, a.map_words, gseg0 - 1);
+                d = (uint32_t)(bits | (bits >> 1) | (bits >> 2));
+            }
+            chg[2 * G::SH + y] = d;
+            act0 += __popc(d);
+        }
+        // Clear this CTA's share of the map the next launch writes.
+        for (size_t i = (size_t)blockIdx.x * G::kThreads + tid; i < map_size; i += (size_t)gridDim.x * G::kThreads)
+            map_clr[i] = 0u;
+        __syncthreads();
+        if (act0) atomicAdd(&s_cnt[3], act0 * (2 * B + 1));
     }
     __syncthreads();
 
@@ -461,35 +535,27 @@ fused_kernel(PassArgs a) {
     c.rows = a.rows;
     c.cols = a.cols;
     c.alpha = a.alpha;
+    c.nchanged = s_cnt;
     for (int t = 0; t < np; ++t) {
         c.in = (t & 1) ? buf1 : buf0;
         c.out = (t & 1) ? buf0 : buf1;
         c.chg_cur = chg + (t % 3) * G::SH;
+        c.cnt_idx = t % 3;
         const uint32_t* chg_prev = chg + ((t + 2) % 3) * G::SH;
         uint32_t* chg_next = chg + ((t + 1) % 3) * G::SH;  // read last in pass t-1; cleared for pass t+1
         for (int i = tid; i < G::SH; i += G::kThreads) chg_next[i] = 0u;
         c.changed_core = false;
-        bool dense = (t == 0);
-        uint32_t act = 0;
-        if (!dense) {
-            if (lane < 8) {
-                const int y = ys + lane;
-#pragma unroll
-                for (int dy = -B; dy <= B; ++dy) {
-                    const uint32_t m = chg_prev[y + dy];
-                    act |= m | (m << 1) | (m >> 1);
-                }
-            }
-            int na = lane < 8 ? __popc(act) : 0;
-#pragma unroll
-            for (int d = 4; d >= 1; d >>= 1) na += __shfl_xor_sync(0xffffffffu, na, d);
-            na = __shfl_sync(0xffffffffu, na, 0);
-            dense = na > G::kDenseAbove;
-        }
+        bool dense;
+        if (t == 0)
+            dense = (L == 0) || (s_cnt[3] > G::kDenseAbove);
+        else
+            dense = s_cnt[(t + 2) % 3] > G::kDenseChanges;
+        // Counter (t + 1) % 3 was last read at the start of pass t - 1.
+        if (tid == 0) s_cnt[(t + 1) % 3] = 0;
         if (dense)
             band_dense<B, T>(c, ys, ws, lane, two_a);
         else
-            band_sparse<B, T>(c, tasks, ys, lane, act, two_a);
+            warp_sparse<B, T>(c, tasks, chg_prev, t == 0, warp, lane, two_a);
         flush_candidates<B, T>(c, lane);
         if (__syncthreads_or(c.changed_core)) cta_mask |= 1u << t;
     }
@@ -509,6 +575,21 @@ fused_kernel(PassArgs a) {
             o.z = h2_to_bytes(q.x, q.y);
             o.w = h2_to_bytes(q.z, q.w);
             *reinterpret_cast<uint4*>(base + (long long)r * a.pitch + cc * 16) = o;
+        }
+    }
+    // Core segments that changed in the last pass -> this launch's map.
+    {
+        const uint32_t* chg_last = chg + ((np - 1) % 3) * G::SH;
+        const int p = x0 / 8;  // global segment of core segment 1
+        for (int r = tid; r < G::TH; r += G::kThreads) {
+            const int gy = y0 + r;
+            if (gy >= a.rows) break;
+            const uint32_t m = (chg_last[G::H + r] >> 1) & ((1u << G::kSegsPerCore) - 1u);
+            if (!m) continue;
+            const unsigned long long v = (unsigned long long)m << (p & 31);
+            uint32_t* row = map_out + (size_t)gy * a.map_words + (p >> 5);
+            atomicOr(row, (uint32_t)v);
+            if (v >> 32) atomicOr(row + 1, (uint32_t)(v >> 32));
         }
     }
     if (tid == 0) finish_launch(a.ctrl, cta_mask, np, gridDim.x);

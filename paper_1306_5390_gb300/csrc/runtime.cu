@@ -27,6 +27,8 @@ struct hgrms_ctx {
     cudaStream_t stream = nullptr;
     uint8_t* canvas[2] = {nullptr, nullptr};
     size_t canvas_bytes = 0;
+    uint32_t* seg_maps = nullptr;  // three segment change maps (fused kernel)
+    size_t seg_map_bytes = 0;
     hg::Ctrl* ctrl = nullptr;
     hg::Ctrl* host_ctrl = nullptr;
     int last_cuda_error = 0;
@@ -113,6 +115,7 @@ struct Plan {
     long long pitch;
     long long crows;
     int launches;
+    int map_words;
 };
 
 int make_plan(hgrms_ctx* h, int rows, int cols, int beta, int max_k, Plan* p) {
@@ -128,6 +131,7 @@ int make_plan(hgrms_ctx* h, int rows, int cols, int beta, int max_k, Plan* p) {
         p->pitch = (need_w + 127) / 128 * 128;
         p->crows = hg::kPadY + (long long)p->tiles_y * p->fe->TH + 16;
         p->launches = (max_k + p->T - 1) / p->T;
+        p->map_words = (p->tiles_x * (p->fe->TW / 8) + 31) / 32 + 1;
     } else {
         p->T = 1;
         p->tiles_x = p->tiles_y = 0;
@@ -135,6 +139,7 @@ int make_plan(hgrms_ctx* h, int rows, int cols, int beta, int max_k, Plan* p) {
         p->pitch = (need_w + 127) / 128 * 128;
         p->crows = hg::kPadY + (long long)rows + 16;
         p->launches = max_k;
+        p->map_words = 0;
     }
     return HGRMS_OK;
 }
@@ -151,6 +156,16 @@ int ensure_canvas(hgrms_ctx* h, size_t bytes) {
         HG_TRY(h, cudaMemsetAsync(h->canvas[i], 0, bytes, h->stream));
     }
     h->canvas_bytes = bytes;
+    return HGRMS_OK;
+}
+
+int ensure_maps(hgrms_ctx* h, size_t bytes) {
+    if (bytes <= h->seg_map_bytes) return HGRMS_OK;
+    if (h->seg_maps) cudaFree(h->seg_maps);
+    h->seg_maps = nullptr;
+    h->seg_map_bytes = 0;
+    HG_TRY(h, cudaMalloc(&h->seg_maps, bytes));
+    h->seg_map_bytes = bytes;
     return HGRMS_OK;
 }
 
@@ -172,6 +187,11 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     if (rc < 0) return rc;
     rc = ensure_canvas(h, (size_t)(p.pitch * p.crows));
     if (rc < 0) return rc;
+    const size_t map_bytes = (size_t)rows * (size_t)p.map_words * sizeof(uint32_t);
+    if (p.fused) {
+        rc = ensure_maps(h, 3 * map_bytes);
+        if (rc < 0) return rc;
+    }
     cudaStream_t s = h->stream;
     uint8_t* ca = h->canvas[0];
     uint8_t* cb = h->canvas[1];
@@ -182,6 +202,8 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
                                     (size_t)cols, (size_t)cols, (size_t)rows, cudaMemcpyHostToDevice, s));
     }
     HG_TRY(h, hg::launch_ctrl_init(h->ctrl, (unsigned)max_k, s));
+    // Map 0 is written by the first launch; the launches clear the others.
+    if (p.fused) HG_TRY(h, cudaMemsetAsync(h->seg_maps, 0, map_bytes, s));
     hg::PassArgs a;
     a.canvas_a = ca;
     a.canvas_b = cb;
@@ -191,6 +213,8 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     a.alpha = alpha;
     a.tiles_x = p.tiles_x;
     a.ctrl = h->ctrl;
+    a.seg_maps = h->seg_maps;
+    a.map_words = p.map_words;
     // Per-launch timing is limited to calls of at most kMaxTimedLaunches launches.
     constexpr int kMaxTimedLaunches = 4096;
     const bool timed = h->opt_timing && p.launches <= kMaxTimedLaunches;
@@ -279,6 +303,7 @@ HG_EXPORT void hgrms_destroy(hgrms_t h) {
         for (int i = 0; i < 2; ++i)
             if (h->canvas[i]) cudaFree(h->canvas[i]);
         if (h->ctrl) cudaFree(h->ctrl);
+        if (h->seg_maps) cudaFree(h->seg_maps);
         if (h->host_ctrl) cudaFreeHost(h->host_ctrl);
         for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     }
