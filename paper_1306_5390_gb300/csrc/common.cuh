@@ -36,11 +36,11 @@ struct PassArgs {
     int alpha;
     int tiles_x;              // tile grid width (fused kernel)
     Ctrl* ctrl;
-    // Segment change maps (fused kernel): three maps of rows x map_words
-    // 32-bit words; bit s of row r = 8-pixel segment s (image columns
-    // [8s, 8s + 8)) changed in the last pass of a launch.  Launch L writes
-    // map L % 3, reads map (L + 2) % 3 and clears map (L + 1) % 3.
-    uint32_t* seg_maps;
+    // Pixel change maps (fused kernel): three bitmaps of rows x map_words
+    // 32-bit words; bit (c & 31) of word c >> 5 of row r = image pixel (r, c)
+    // changed in the last pass of a launch.  Launch L writes map L % 3,
+    // reads map (L + 2) % 3 and clears map (L + 1) % 3.
+    uint32_t* chg_maps;
     int map_words;            // words per image row
 };
 

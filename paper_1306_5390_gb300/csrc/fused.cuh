@@ -24,10 +24,11 @@
 //    in pass t-1, p's output in pass t equals its output in pass t-1, i.e.
 //    its current value.  With two ping-pong buffers, the buffer written by
 //    pass t already holds pass t-2's values, which equal pass t-1's at every
-//    pixel that did not change in pass t-1.  So after the first pass of a
-//    launch (which writes the whole tile), a pass only needs to recompute
-//    8-pixel row segments within beta of a segment that changed in the
-//    previous pass; all other segments are already correct in both buffers.
+//    pixel that did not change in pass t-1.  So once few pixels change, a
+//    pass only evaluates the windows around the pixels the previous pass
+//    changed (a "list pass"); every other pixel is already correct in both
+//    buffers.  Between launches the changed pixels of a launch's last pass
+//    travel in a global bitmap, one bit per pixel.
 //
 // Packed closed-neighbour test.  Pixel values are stored in shared memory as
 // fp16 (exact for 0..255), two pixels per 32-bit word.  For a centre value
@@ -38,13 +39,12 @@
 // saturation and one add count two pixels' neighbours.  A count of 0 or 1 is
 // an fp16 bit pattern with bit 14 clear; 2 and above have it set.
 //
-// Work layout: a pass computes rows [R0, R0 + 64) and 32 segments of 8
-// pixels per row (columns [8, 264)).  In a dense pass warp w walks rows
-// [R0 + 8w, R0 + 8w + 8) with a register ring of the 2 beta + 1 window rows,
-// lane l owning segment l.  A sparse pass builds a CTA-wide list of the
-// active (row, segment) pairs and every lane of every warp takes one.
-// Candidate pixels (at most one closed neighbour) are appended to a per-warp
-// list and evaluated exactly, one per lane.
+// Work layout: a pass computes rows [R0, R0 + 64) and columns [8, 264).  In
+// a dense pass warp w walks rows [R0 + 8w, R0 + 8w + 8) with a register ring
+// of the 2 beta + 1 window rows, lane l owning the 8 pixels at columns
+// [8 + 8l, 16 + 8l); candidate pixels (at most one closed neighbour) are
+// appended to a per-warp list and evaluated exactly, one per lane.  A list
+// pass spreads (changed pixel, window offset) pairs over all threads.
 #pragma once
 
 #include <cuda_fp16.h>
@@ -56,7 +56,7 @@ template <int B, int T>
 struct FusedGeo {
     static constexpr int kThreads = 256;
     static constexpr int kWarps = kThreads / 32;
-    static constexpr int kRows = 8;                  // rows per warp band
+    static constexpr int kRows = 8;                  // rows per warp band (dense passes)
     static constexpr int TW = 240;                   // core tile width (pixels)
     static constexpr int RN = kRows * kWarps;        // rows computed per pass (64)
     static constexpr int TH = RN - 2 * (T - 1) * B;  // core tile height
@@ -66,24 +66,25 @@ struct FusedGeo {
     static constexpr int SWW = SW / 2;               // 32-bit words per tile row
     static constexpr int R0 = H - (T - 1) * B;       // first computed row (= B)
     static constexpr int C0 = kPadX - 8;             // first computed column
-    static constexpr int kSegs = 32 * RN;            // 8-pixel row segments computed per pass
-    static constexpr int kSegsPerCore = TW / 8;      // core segments per row (30)
-    static constexpr int kCandCap = 8 * 256;         // per-warp candidate list: a whole band
-    static constexpr int kDenseAbove = kSegs * 3 / 8;  // active segments above which a pass runs dense
-    static constexpr int kDenseChanges = 96;         // changed pixels in pass t-1 above which pass t runs dense
+    static constexpr int CN = 256;                   // computed columns
+    static constexpr int P = (2 * B + 1) * (2 * B + 1);
+    static constexpr int kCandCap = 1024;            // per-warp candidate list (half a band)
+    static constexpr int kListCap = 2048;            // changed pixels kept per pass
+    static constexpr int kListEvalMax = 2048;        // list-pass evaluations above which a pass runs dense
+    static constexpr int kMarkWords = (SH * SW + 31) / 32;
     // shared memory layout (bytes)
     static constexpr size_t kBufBytes = (size_t)SH * SW * sizeof(__half);
-    static constexpr size_t kChgOff = 2 * kBufBytes;
-    static constexpr size_t kCandOff = kChgOff + 3ull * SH * sizeof(uint32_t);
-    static constexpr size_t kTaskOff = kCandOff + (size_t)kWarps * kCandCap * sizeof(uint16_t);
-    static constexpr size_t kCntOff = kTaskOff + (size_t)kWarps * 256;
+    static constexpr size_t kCandOff = 2 * kBufBytes;
+    static constexpr size_t kListOff = kCandOff + (size_t)kWarps * kCandCap * sizeof(uint16_t);
+    static constexpr size_t kMarkOff = kListOff + 2ull * kListCap * sizeof(uint16_t);
+    static constexpr size_t kCntOff = kMarkOff + 2ull * kMarkWords * sizeof(uint32_t);
     static constexpr size_t kSmem = kCntOff + 4 * sizeof(int);
     // Lanes 0..31 cover columns [C0, C0 + 256): results within T*beta of
     // those edges may use wrong horizontal neighbours, so T*beta <= 8 keeps
     // the core [kPadX, kPadX + TW) exact after T passes.
     static_assert(T * B <= 8, "fused halo exceeds the computed margin");
     static_assert(TH >= 16, "tile too short");
-    static_assert(SH <= 127 && SW <= 511, "candidate encoding");
+    static_assert(SH * SW < 65536, "pixel index encoding");
     static_assert(C0 + 8 * 32 == kPadX + TW + 8, "strip layout");
 };
 
@@ -147,24 +148,6 @@ __device__ __forceinline__ void load_row_shfl(const uint32_t* __restrict__ rowp,
     for (int i = 0; i < WB; ++i) {
         w[WB - 1 - i] = __shfl_up_sync(0xffffffffu, cw[3 - i], 1);
         w[WB + 4 + i] = __shfl_down_sync(0xffffffffu, cw[i], 1);
-    }
-    make_pairs<B>(w, r);
-}
-
-// Lane-independent form (sparse passes): every word from shared memory.
-template <int B>
-__device__ __forceinline__ void load_row_lds(const uint32_t* __restrict__ rowp, Row<B>& r) {
-    constexpr int WB = Row<B>::WB;
-    const uint4 c = *reinterpret_cast<const uint4*>(rowp);
-    uint32_t w[4 + 2 * WB];
-    w[WB + 0] = c.x;
-    w[WB + 1] = c.y;
-    w[WB + 2] = c.z;
-    w[WB + 3] = c.w;
-#pragma unroll
-    for (int i = 0; i < WB; ++i) {
-        w[WB - 1 - i] = rowp[-1 - i];
-        w[WB + 4 + i] = rowp[4 + i];
     }
     make_pairs<B>(w, r);
 }
@@ -243,39 +226,55 @@ struct PassCtx {
     using G = FusedGeo<B, T>;
     const uint32_t* in;
     uint32_t* out;
-    uint32_t* chg_cur;   // change map written by this pass (bit l of row y: segment l changed)
-    uint16_t* cand;      // this warp's candidate list
+    uint16_t* cand;      // this warp's candidate list (dense passes)
     int ncand;           // entries in the list (warp-uniform)
+    uint16_t* list;      // changed pixels of this pass (index y * SW + x)
+    int* nlist;          // its counter (may exceed kListCap: overflow)
     int x0, y0, rows, cols, alpha;
-    int* nchanged;       // shared counters of changed pixels per pass (3, rotating)
-    int cnt_idx;         // counter of this pass
     bool changed_core;   // this lane saw a core pixel change
 };
 
-// Evaluate and clear the warp's candidate list.
+__device__ __forceinline__ bool in_core_px(int y, int x, int H, int TH, int TW) {
+    return y >= H && y < H + TH && x >= kPadX && x < kPadX + TW;
+}
+
+// Evaluate and clear the warp's candidate list (dense passes): replaced
+// pixels are written to the output buffer and recorded as changed.
 template <int B, int T>
 __device__ __forceinline__ void flush_candidates(PassCtx<B, T>& c, const int lane) {
     using G = FusedGeo<B, T>;
     __syncwarp();
     const __half* hin = reinterpret_cast<const __half*>(c.in);
     __half* hout = reinterpret_cast<__half*>(c.out);
-    int nch = 0;
-    for (int i = lane; i < c.ncand; i += 32) {
-        const uint32_t e = c.cand[i];
-        const int y = (int)(e >> 9), x = (int)(e & 511u);
-        const int gx = c.x0 + x - kPadX, gy = c.y0 + y - G::H;
-        if (gy < B || gy >= c.rows - B || gx < B || gx >= c.cols - B) continue;
-        const int v = exact_replacement<B, G::SW>(hin, y, x, c.alpha);
-        if (v < 0) continue;
-        const __half hv = __int2half_rn(v);
-        if (__half_as_ushort(hv) == __half_as_ushort(hin[y * G::SW + x])) continue;
-        hout[y * G::SW + x] = hv;
-        atomicOr(&c.chg_cur[y], 1u << ((x - G::C0) >> 3));
-        ++nch;
-        if (y >= G::H && y < G::H + G::TH && x >= kPadX && x < kPadX + G::TW) c.changed_core = true;
+    for (int base = 0; base < c.ncand; base += 32) {
+        const int i = base + lane;
+        bool ch = false;
+        uint32_t q = 0;
+        if (i < c.ncand) {
+            q = c.cand[i];
+            const int y = (int)(q / G::SW), x = (int)(q - (uint32_t)y * G::SW);
+            const int gx = c.x0 + x - kPadX, gy = c.y0 + y - G::H;
+            if (gy >= B && gy < c.rows - B && gx >= B && gx < c.cols - B) {
+                const int v = exact_replacement<B, G::SW>(hin, y, x, c.alpha);
+                if (v >= 0) {
+                    const __half hv = __int2half_rn(v);
+                    if (__half_as_ushort(hv) != __half_as_ushort(hin[q])) {
+                        hout[q] = hv;
+                        ch = true;
+                        if (in_core_px(y, x, G::H, G::TH, G::TW)) c.changed_core = true;
+                    }
+                }
+            }
+        }
+        // record the changed pixels (one shared atomic per warp)
+        const uint32_t bal = __ballot_sync(0xffffffffu, ch);
+        if (bal) {
+            int pos = 0;
+            if (lane == 0) pos = atomicAdd(c.nlist, __popc(bal));
+            pos = __shfl_sync(0xffffffffu, pos, 0) + __popc(bal & ((1u << lane) - 1u));
+            if (ch && pos < G::kListCap) c.list[pos] = (uint16_t)q;
+        }
     }
-    nch = __reduce_add_sync(0xffffffffu, nch);
-    if (lane == 0 && nch) atomicAdd(&c.nchanged[c.cnt_idx], nch);
     __syncwarp();
     c.ncand = 0;
 }
@@ -292,9 +291,26 @@ __device__ __forceinline__ int warp_excl_scan(const int lane, const int n, int* 
     return incl - n;
 }
 
-// Dense pass over the warp's 8-row band.  Candidate bits of the band are
-// gathered in one 64-bit mask per lane (bit 8r + i: row r, pixel i of the
-// lane's segment) and appended to the (empty) warp list in one step.
+// Append candidate bits (bit 8r + i: row ys + r, pixel x + i) to the warp list.
+template <int B, int T>
+__device__ __forceinline__ void append_bits(PassCtx<B, T>& c, const int lane, uint32_t m, const int ys,
+                                            const int x) {
+    using G = FusedGeo<B, T>;
+    if (!__any_sync(0xffffffffu, m != 0u)) return;
+    int total;
+    const int off0 = warp_excl_scan(lane, __popc(m), &total);
+    if (c.ncand + total > G::kCandCap) flush_candidates<B, T>(c, lane);
+    int off = c.ncand + off0;
+    while (m) {
+        const int b = __ffs(m) - 1;
+        c.cand[off++] = (uint16_t)((ys + (b >> 3)) * G::SW + x + (b & 7));
+        m &= m - 1;
+    }
+    c.ncand += total;
+}
+
+// Dense pass over the warp's 8-row band: every pixel's closed neighbours are
+// counted with the packed test; candidates go to the warp list.
 template <int B, int T>
 __device__ __forceinline__ void band_dense(PassCtx<B, T>& c, const int ys, const int ws, const int lane,
                                            const __half2 two_a) {
@@ -335,112 +351,46 @@ __device__ __forceinline__ void band_dense(PassCtx<B, T>& c, const int ys, const
         if ((all & 0x40004000u) != 0x40004000u)
             m64 |= (unsigned long long)candidate_mask(cnt) << (8 * r);
     }
-    if (__any_sync(0xffffffffu, m64 != 0ull)) {
-        int total;
-        int off = warp_excl_scan(lane, __popcll(m64), &total);
-        const uint32_t x = (uint32_t)(2 * ws);
-        while (m64) {
-            const int b = __ffsll((long long)m64) - 1;
-            c.cand[off++] = (uint16_t)((((uint32_t)(ys + (b >> 3))) << 9) | (x + (uint32_t)(b & 7)));
-            m64 &= m64 - 1ull;
-        }
-        c.ncand = total;
-    }
+    append_bits<B, T>(c, lane, (uint32_t)m64, ys, 2 * ws);
+    append_bits<B, T>(c, lane, (uint32_t)(m64 >> 32), ys + 4, 2 * ws);
 }
 
-// One (row, segment) of a sparse pass, computed by one lane.
+// List pass: only pixels within beta of a pixel that changed in the
+// previous pass can change now.  Each (changed pixel, window offset) pair
+// claims its pixel in the mark bitmap; the claimer evaluates it exactly
+// (Algorithm 2) from `in` and writes it to `out`.
 template <int B, int T>
-__device__ __forceinline__ uint32_t segment_lds(PassCtx<B, T>& c, const int y, const int ws, const __half2 two_a) {
+__device__ __forceinline__ void list_pass(PassCtx<B, T>& c, const uint16_t* prev, const int nprev, uint32_t* mark,
+                                          const int tid) {
     using G = FusedGeo<B, T>;
-    Row<B> rr;
-    __half2 cp[4], cnt[4];
-    uint4 centre;
-    load_row_lds<B>(c.in + y * G::SWW + ws, rr);
-    centre_setup<B>(rr, cp, cnt, centre);
-    count_row<B>(rr, 0, cp, two_a, cnt);
-#pragma unroll
-    for (int dy = -B; dy <= B; ++dy) {
-        if (dy == 0) continue;
-        load_row_lds<B>(c.in + (y + dy) * G::SWW + ws, rr);
-        count_row<B>(rr, dy, cp, two_a, cnt);
-    }
-    *reinterpret_cast<uint4*>(c.out + y * G::SWW + ws) = centre;
-    const uint32_t all = h2u(cnt[0]) & h2u(cnt[1]) & h2u(cnt[2]) & h2u(cnt[3]);
-    return ((all & 0x40004000u) != 0x40004000u) ? candidate_mask(cnt) : 0u;
-}
-
-// Sparse pass: warp w takes the active segments of its interleaved rows
-// R0 + w + 8r (r = 0..7), one segment per lane.  A segment is active when a
-// segment within beta rows and one segment sideways changed in the previous
-// pass (`predilated`: the map already includes the sideways neighbours).
-template <int B, int T>
-__device__ __forceinline__ void warp_sparse(PassCtx<B, T>& c, uint8_t* tasks, const uint32_t* chg_prev,
-                                            const bool predilated, const int warp, const int lane,
-                                            const __half2 two_a) {
-    using G = FusedGeo<B, T>;
-    uint32_t act = 0;
-    if (lane < 8) {
-        const int y = G::R0 + warp + 8 * lane;
-#pragma unroll
-        for (int dy = -B; dy <= B; ++dy) {
-            const uint32_t m = chg_prev[y + dy];
-            act |= predilated ? m : (m | (m << 1) | (m >> 1));
+    const __half* hin = reinterpret_cast<const __half*>(c.in);
+    __half* hout = reinterpret_cast<__half*>(c.out);
+    const int npairs = nprev * G::P;
+    for (int i = tid; i < npairs; i += G::kThreads) {
+        const int e = i / G::P;
+        const int o = i - e * G::P;
+        const int dy = o / (2 * B + 1) - B, dx = o % (2 * B + 1) - B;
+        const int p = prev[e];
+        const int py = p / G::SW;
+        const int y = py + dy, x = p - py * G::SW + dx;
+        if (y < G::R0 || y >= G::R0 + G::RN || x < G::C0 || x >= G::C0 + G::CN) continue;
+        const int q = y * G::SW + x;
+        const uint32_t bit = 1u << (q & 31);
+        if (atomicOr(&mark[q >> 5], bit) & bit) continue;  // someone else evaluates q
+        const __half old = hin[q];
+        __half nv = old;
+        const int gx = c.x0 + x - kPadX, gy = c.y0 + y - G::H;
+        if (gy >= B && gy < c.rows - B && gx >= B && gx < c.cols - B) {
+            const int v = exact_replacement<B, G::SW>(hin, y, x, c.alpha);
+            if (v >= 0) nv = __int2half_rn(v);
+        }
+        hout[q] = nv;
+        if (__half_as_ushort(nv) != __half_as_ushort(old)) {
+            const int pos = atomicAdd(c.nlist, 1);
+            if (pos < G::kListCap) c.list[pos] = (uint16_t)q;
+            if (in_core_px(y, x, G::H, G::TH, G::TW)) c.changed_core = true;
         }
     }
-    const int n = __popc(act);
-    int incl = n;
-#pragma unroll
-    for (int d = 1; d < 8; d <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += v;
-    }
-    const int total = __shfl_sync(0xffffffffu, incl, 7);
-    if (lane < 8) {
-        int off = incl - n;
-        uint32_t m = act;
-        while (m) {
-            const int b = __ffs(m) - 1;
-            tasks[off++] = (uint8_t)((lane << 5) | b);
-            m &= m - 1;
-        }
-    }
-    __syncwarp();
-    for (int base = 0; base < total; base += 32) {
-        const int i = base + lane;
-        uint32_t mask = 0;
-        int y = 0, x = 0;
-        if (i < total) {
-            const int t = tasks[i];
-            y = G::R0 + warp + 8 * (t >> 5);
-            const int ws = G::C0 / 2 + 4 * (t & 31);
-            x = 2 * ws;
-            mask = segment_lds<B, T>(c, y, ws, two_a);
-        }
-        if (__any_sync(0xffffffffu, mask != 0u)) {
-            if (c.ncand + 32 * 8 > G::kCandCap) flush_candidates<B, T>(c, lane);
-            int tot;
-            int off = c.ncand + warp_excl_scan(lane, __popc(mask), &tot);
-            const uint32_t base_e = ((uint32_t)y << 9) | (uint32_t)x;
-            while (mask) {
-                const int b = __ffs(mask) - 1;
-                c.cand[off++] = (uint16_t)(base_e + (uint32_t)b);
-                mask &= mask - 1;
-            }
-            c.ncand += tot;
-        }
-    }
-}
-
-// Bits [start, start + 64) of a row of the segment change map (positions
-// outside [0, 32 * nwords) read as 0; start may be negative).
-__device__ __forceinline__ unsigned long long map_bits(const uint32_t* __restrict__ row, int nwords, int start) {
-    const int w0 = start >= 0 ? (start >> 5) : -((31 - start) >> 5);
-    const int sh = start - 32 * w0;
-    const uint32_t a = (w0 >= 0 && w0 < nwords) ? __ldcg(row + w0) : 0u;
-    const uint32_t b = (w0 + 1 >= 0 && w0 + 1 < nwords) ? __ldcg(row + w0 + 1) : 0u;
-    const uint32_t c = (w0 + 2 >= 0 && w0 + 2 < nwords) ? __ldcg(row + w0 + 2) : 0u;
-    const unsigned long long lo = ((unsigned long long)b << 32) | a;
-    return sh ? ((lo >> sh) | ((unsigned long long)c << (64 - sh))) : lo;
 }
 
 template <int B, int T>
@@ -468,20 +418,19 @@ fused_kernel(PassArgs a) {
     const int x0 = tx * G::TW, y0 = ty * G::TH;
     uint32_t* buf0 = reinterpret_cast<uint32_t*>(smem);
     uint32_t* buf1 = reinterpret_cast<uint32_t*>(smem + G::kBufBytes);
-    uint32_t* chg = reinterpret_cast<uint32_t*>(smem + G::kChgOff);  // 3 maps of SH rows
     uint16_t* cand = reinterpret_cast<uint16_t*>(smem + G::kCandOff) + warp * G::kCandCap;
-    uint8_t* tasks = smem + G::kTaskOff + warp * 256;
-    int* s_cnt = reinterpret_cast<int*>(smem + G::kCntOff);  // [0..2]: changed pixels per pass; [3]: pass-0 activity
+    uint16_t* lists = reinterpret_cast<uint16_t*>(smem + G::kListOff);  // 2 lists: pass t uses t & 1
+    uint32_t* marks = reinterpret_cast<uint32_t*>(smem + G::kMarkOff);  // 2 bitmaps: pass t uses t & 1
+    int* s_cnt = reinterpret_cast<int*>(smem + G::kCntOff);             // list counters, pass t uses t % 3
     const size_t map_size = (size_t)a.rows * (size_t)a.map_words;
-    uint32_t* map_out = a.seg_maps + (size_t)(L % 3u) * map_size;
-    const uint32_t* map_in = a.seg_maps + (size_t)((L + 2u) % 3u) * map_size;
-    uint32_t* map_clr = a.seg_maps + (size_t)((L + 1u) % 3u) * map_size;
-    const int gseg0 = x0 / 8 - 1;  // global segment of tile segment 0
+    uint32_t* map_out = a.chg_maps + (size_t)(L % 3u) * map_size;
+    const uint32_t* map_in = a.chg_maps + (size_t)((L + 2u) % 3u) * map_size;
+    uint32_t* map_clr = a.chg_maps + (size_t)((L + 1u) % 3u) * map_size;
 
     // Tile with halo: image rows [y0 - H, y0 + TH + H), columns [x0 - 16,
     // x0 + TW + 16); always inside the canvas.  Bytes -> fp16 pairs, into
-    // both buffers (so that a sparse first pass finds every segment it does
-    // not recompute already in its output buffer).
+    // both buffers (a list pass leaves unevaluated pixels as they are in its
+    // output buffer, so that buffer must start equal to the input).
     {
         const uint8_t* base = src + (long long)(kPadY + y0 - G::H) * a.pitch + x0;
         constexpr int CH = G::SW / 16;
@@ -500,28 +449,34 @@ fused_kernel(PassArgs a) {
             d1[0] = lo;
             d1[1] = hi;
         }
+        for (int i = tid; i < 2 * G::kMarkWords; i += G::kThreads) marks[i] = 0u;
         if (tid < 4) s_cnt[tid] = 0;
-        // Pass 0 reads map 2: the previous launch's last-pass changes, each
-        // segment widened by one segment to both sides.
-        int act0 = 0;
-        for (int y = tid; y < G::SH; y += G::kThreads) {
-            chg[y] = 0u;  // written by pass 0
-            uint32_t d = 0u;
-            const int gy = y0 - G::H + y;
-            if (L > 0 && gy >= 0 && gy < a.rows) {
-                const unsigned long long bits = map_bits(map_in + (size_t)gy * a.map_words, a.map_words, gseg0 - 1);
-                d = (uint32_t)(bits | (bits >> 1) | (bits >> 2));
-            }
-            chg[2 * G::SH + y] = d;
-            act0 += __popc(d);
-        }
         // Clear this CTA's share of the map the next launch writes.
         for (size_t i = (size_t)blockIdx.x * G::kThreads + tid; i < map_size; i += (size_t)gridDim.x * G::kThreads)
             map_clr[i] = 0u;
-        __syncthreads();
-        if (act0) atomicAdd(&s_cnt[3], act0 * (2 * B + 1));
     }
     __syncthreads();
+    // Pass 0's "previous pass": the pixels the previous launch's last pass
+    // changed (global map), listed in list 1 / counter 2.
+    if (L > 0) {
+        const int wlo = (x0 - kPadX) >> 5;  // floor division (x0 - 16 >= -16)
+        const int nw = ((x0 + G::TW + kPadX - 1) >> 5) - wlo + 1;
+        for (int i = tid; i < G::SH * nw; i += G::kThreads) {
+            const int y = i / nw, w = wlo + (i - y * nw);
+            const int gy = y0 - G::H + y;
+            if (gy < 0 || gy >= a.rows || w < 0 || w >= a.map_words) continue;
+            uint32_t bits = __ldcg(map_in + (size_t)gy * a.map_words + w);
+            while (bits) {
+                const int b = __ffs(bits) - 1;
+                bits &= bits - 1;
+                const int x = 32 * w + b - x0 + kPadX;
+                if (x < 0 || x >= G::SW) continue;
+                const int pos = atomicAdd(&s_cnt[2], 1);
+                if (pos < G::kListCap) lists[G::kListCap + pos] = (uint16_t)(y * G::SW + x);
+            }
+        }
+        __syncthreads();
+    }
 
     unsigned cta_mask = 0;
     const __half2 two_a = __float2half2_rn(2.f * (float)a.alpha);
@@ -535,28 +490,26 @@ fused_kernel(PassArgs a) {
     c.rows = a.rows;
     c.cols = a.cols;
     c.alpha = a.alpha;
-    c.nchanged = s_cnt;
     for (int t = 0; t < np; ++t) {
         c.in = (t & 1) ? buf1 : buf0;
         c.out = (t & 1) ? buf0 : buf1;
-        c.chg_cur = chg + (t % 3) * G::SH;
-        c.cnt_idx = t % 3;
-        const uint32_t* chg_prev = chg + ((t + 2) % 3) * G::SH;
-        uint32_t* chg_next = chg + ((t + 1) % 3) * G::SH;  // read last in pass t-1; cleared for pass t+1
-        for (int i = tid; i < G::SH; i += G::kThreads) chg_next[i] = 0u;
+        c.list = lists + (t & 1) * G::kListCap;
+        c.nlist = &s_cnt[t % 3];
+        const uint16_t* prev = lists + ((t + 1) & 1) * G::kListCap;
+        const int nprev = s_cnt[(t + 2) % 3];
         c.changed_core = false;
-        bool dense;
-        if (t == 0)
-            dense = (L == 0) || (s_cnt[3] > G::kDenseAbove);
-        else
-            dense = s_cnt[(t + 2) % 3] > G::kDenseChanges;
-        // Counter (t + 1) % 3 was last read at the start of pass t - 1.
+        // Counter (t + 1) % 3 was last read at the start of pass t - 1; bitmap
+        // (t + 1) & 1 was last used in pass t - 1.
         if (tid == 0) s_cnt[(t + 1) % 3] = 0;
-        if (dense)
+        uint32_t* mark_next = marks + ((t + 1) & 1) * G::kMarkWords;
+        for (int i = tid; i < G::kMarkWords; i += G::kThreads) mark_next[i] = 0u;
+        const bool dense = (t == 0 && L == 0) || nprev > G::kListCap || nprev * G::P > G::kListEvalMax;
+        if (dense) {
             band_dense<B, T>(c, ys, ws, lane, two_a);
-        else
-            warp_sparse<B, T>(c, tasks, chg_prev, t == 0, warp, lane, two_a);
-        flush_candidates<B, T>(c, lane);
+            flush_candidates<B, T>(c, lane);
+        } else {
+            list_pass<B, T>(c, prev, nprev, marks + (t & 1) * G::kMarkWords, tid);
+        }
         if (__syncthreads_or(c.changed_core)) cta_mask |= 1u << t;
     }
     const uint32_t* fin = (np & 1) ? buf1 : buf0;
@@ -577,19 +530,31 @@ fused_kernel(PassArgs a) {
             *reinterpret_cast<uint4*>(base + (long long)r * a.pitch + cc * 16) = o;
         }
     }
-    // Core segments that changed in the last pass -> this launch's map.
+    // The last pass's changed core pixels -> this launch's map (all core
+    // pixels when the list overflowed: a superset is always safe).
     {
-        const uint32_t* chg_last = chg + ((np - 1) % 3) * G::SH;
-        const int p = x0 / 8;  // global segment of core segment 1
-        for (int r = tid; r < G::TH; r += G::kThreads) {
-            const int gy = y0 + r;
-            if (gy >= a.rows) break;
-            const uint32_t m = (chg_last[G::H + r] >> 1) & ((1u << G::kSegsPerCore) - 1u);
-            if (!m) continue;
-            const unsigned long long v = (unsigned long long)m << (p & 31);
-            uint32_t* row = map_out + (size_t)gy * a.map_words + (p >> 5);
-            atomicOr(row, (uint32_t)v);
-            if (v >> 32) atomicOr(row + 1, (uint32_t)(v >> 32));
+        const int nlast = s_cnt[(np - 1) % 3];
+        const uint16_t* last = lists + ((np - 1) & 1) * G::kListCap;
+        if (nlast <= G::kListCap) {
+            for (int i = tid; i < nlast; i += G::kThreads) {
+                const int q = last[i];
+                const int y = q / G::SW, x = q - y * G::SW;
+                if (!in_core_px(y, x, G::H, G::TH, G::TW)) continue;
+                const int gy = y0 + y - G::H, gx = x0 + x - kPadX;
+                if (gy >= a.rows || gx >= a.cols) continue;
+                atomicOr(map_out + (size_t)gy * a.map_words + (gx >> 5), 1u << (gx & 31));
+            }
+        } else {
+            for (int r = tid; r < G::TH; r += G::kThreads) {
+                const int gy = y0 + r;
+                if (gy >= a.rows) break;
+                uint32_t* row = map_out + (size_t)gy * a.map_words;
+                for (int gx = x0; gx < x0 + G::TW; gx += 32 - (gx & 31)) {
+                    const int n = min(32 - (gx & 31), x0 + G::TW - gx);
+                    const uint32_t m = (n == 32 ? 0xffffffffu : ((1u << n) - 1u)) << (gx & 31);
+                    atomicOr(row + (gx >> 5), m);
+                }
+            }
         }
     }
     if (tid == 0) finish_launch(a.ctrl, cta_mask, np, gridDim.x);

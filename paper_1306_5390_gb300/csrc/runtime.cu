@@ -27,8 +27,8 @@ struct hgrms_ctx {
     cudaStream_t stream = nullptr;
     uint8_t* canvas[2] = {nullptr, nullptr};
     size_t canvas_bytes = 0;
-    uint32_t* seg_maps = nullptr;  // three segment change maps (fused kernel)
-    size_t seg_map_bytes = 0;
+    uint32_t* chg_maps = nullptr;  // three pixel change bitmaps (fused kernel)
+    size_t chg_map_bytes = 0;
     hg::Ctrl* ctrl = nullptr;
     hg::Ctrl* host_ctrl = nullptr;
     int last_cuda_error = 0;
@@ -131,7 +131,7 @@ int make_plan(hgrms_ctx* h, int rows, int cols, int beta, int max_k, Plan* p) {
         p->pitch = (need_w + 127) / 128 * 128;
         p->crows = hg::kPadY + (long long)p->tiles_y * p->fe->TH + 16;
         p->launches = (max_k + p->T - 1) / p->T;
-        p->map_words = (p->tiles_x * (p->fe->TW / 8) + 31) / 32 + 1;
+        p->map_words = (p->tiles_x * p->fe->TW + 31) / 32 + 2;
     } else {
         p->T = 1;
         p->tiles_x = p->tiles_y = 0;
@@ -160,12 +160,12 @@ int ensure_canvas(hgrms_ctx* h, size_t bytes) {
 }
 
 int ensure_maps(hgrms_ctx* h, size_t bytes) {
-    if (bytes <= h->seg_map_bytes) return HGRMS_OK;
-    if (h->seg_maps) cudaFree(h->seg_maps);
-    h->seg_maps = nullptr;
-    h->seg_map_bytes = 0;
-    HG_TRY(h, cudaMalloc(&h->seg_maps, bytes));
-    h->seg_map_bytes = bytes;
+    if (bytes <= h->chg_map_bytes) return HGRMS_OK;
+    if (h->chg_maps) cudaFree(h->chg_maps);
+    h->chg_maps = nullptr;
+    h->chg_map_bytes = 0;
+    HG_TRY(h, cudaMalloc(&h->chg_maps, bytes));
+    h->chg_map_bytes = bytes;
     return HGRMS_OK;
 }
 
@@ -203,7 +203,7 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     }
     HG_TRY(h, hg::launch_ctrl_init(h->ctrl, (unsigned)max_k, s));
     // Map 0 is written by the first launch; the launches clear the others.
-    if (p.fused) HG_TRY(h, cudaMemsetAsync(h->seg_maps, 0, map_bytes, s));
+    if (p.fused) HG_TRY(h, cudaMemsetAsync(h->chg_maps, 0, map_bytes, s));
     hg::PassArgs a;
     a.canvas_a = ca;
     a.canvas_b = cb;
@@ -213,7 +213,7 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     a.alpha = alpha;
     a.tiles_x = p.tiles_x;
     a.ctrl = h->ctrl;
-    a.seg_maps = h->seg_maps;
+    a.chg_maps = h->chg_maps;
     a.map_words = p.map_words;
     // Per-launch timing is limited to calls of at most kMaxTimedLaunches launches.
     constexpr int kMaxTimedLaunches = 4096;
@@ -303,7 +303,7 @@ HG_EXPORT void hgrms_destroy(hgrms_t h) {
         for (int i = 0; i < 2; ++i)
             if (h->canvas[i]) cudaFree(h->canvas[i]);
         if (h->ctrl) cudaFree(h->ctrl);
-        if (h->seg_maps) cudaFree(h->seg_maps);
+        if (h->chg_maps) cudaFree(h->chg_maps);
         if (h->host_ctrl) cudaFreeHost(h->host_ctrl);
         for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     }
