@@ -47,7 +47,8 @@ def parse_args(argv=None):
     p.add_argument("--workload", choices=("8192", "256"), default="8192")
     p.add_argument("--betas", default="1,2,3")
     p.add_argument("--passes", type=int, default=0, help="fused passes per launch (0 = built-in)")
-    p.add_argument("--kernel", type=int, default=0, help="0 fused, 1 unfused")
+    p.add_argument("--kernel", type=int, default=0,
+                   help="0 fused tile launch + list passes (default), 1 unfused, 2 fused tile launches only")
     p.add_argument("--size", type=int, default=8192, help="side of the square image (8192 workload)")
     p.add_argument("--cpu-rows", type=int, default=128, help="rows of the oracle baseline sample")
     p.add_argument("--ref-rows", type=int, default=64, help="rows of each reference-arm step")
@@ -166,15 +167,19 @@ def run_ours(args, rank, world, local):
         for i, b in enumerate(betas):
             k = d.denoise(work[i], alpha, b, max_k)
             st = d.stats()
-            per_beta[b]["k"] = k
-            per_beta[b]["converged"] = d.converged()
+            pb = per_beta[b]
+            pb["k"] = k
+            pb["converged"] = d.converged()
             for key in ("kernel_ms", "idle_kernel_ms"):
-                per_beta[b][key] += st[key]
-            for key in ("work_launches", "launches", "passes_executed"):
-                per_beta[b][key] += st[key]
-            per_beta[b]["T"] = st["passes_per_launch"]
-            per_beta[b]["ctas"] = st["ctas_per_launch"]
-            per_beta[b]["calls"] += 1
+                pb[key] += st[key]
+            for key in ("work_launches", "launches", "passes_executed", "evals_fused", "evals_list"):
+                pb[key] += st[key]
+            for ms, kind in d.launch_times()[: st["work_launches"]]:
+                pb["ms_by_kind"][kind] += ms
+                pb["n_by_kind"][kind] += 1
+            pb["T"] = st["passes_per_launch"]
+            pb["ctas"] = st["ctas_per_launch"]
+            pb["calls"] += 1
 
     def fresh():
         for t in work:
@@ -184,7 +189,8 @@ def run_ours(args, rank, world, local):
 
     def new_acc():
         return {b: dict(k=0, converged=False, kernel_ms=0.0, idle_kernel_ms=0.0, work_launches=0, launches=0,
-                        passes_executed=0, T=0, ctas=0, calls=0) for b in betas}
+                        passes_executed=0, evals_fused=0, evals_list=0, ms_by_kind=[0.0, 0.0, 0.0],
+                        n_by_kind=[0, 0, 0], T=0, ctas=0, calls=0) for b in betas}
 
     for _ in range(args.warmup):
         fresh()
@@ -242,45 +248,54 @@ def run_ours(args, rank, world, local):
 
     peaks, peak_kind = measured_peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
+    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
+    alu_peak = sms * 128 * sm_mhz * 1e6 / 1e9  # Gop/s: one 32-bit op per lane per clock
+    kind_name = {0: "fused_kernel", 1: "list_kernel", 2: "plain_kernel"}
     per_beta_out = {}
-    dom_b, dom_ms = None, -1.0
+    kernels = []  # (total ms, name, beta, tests, launches)
     for b in betas:
         a = acc[b]
         taps = (2 * b + 1) ** 2 - 1
-        tests = taps * rows * cols * a["passes_executed"]
+        calls = max(1, a["calls"])
+        ev = {0: a["evals_fused"], 1: a["evals_list"], 2: a["passes_executed"] * rows * cols}
         per_beta_out[str(b)] = dict(
             k=a["k"], converged=bool(a["converged"]), passes_per_launch=a["T"],
-            work_launches_per_call=a["work_launches"] / max(1, a["calls"]),
-            kernel_ms_per_call=a["kernel_ms"] / max(1, a["calls"]),
-            idle_launch_ms_per_call=a["idle_kernel_ms"] / max(1, a["calls"]),
-            neighbour_tests_per_s=tests / (a["kernel_ms"] * 1e-3) if a["kernel_ms"] > 0 else None,
+            work_launches_per_call=a["work_launches"] / calls,
+            kernel_ms_per_call=a["kernel_ms"] / calls,
+            idle_launch_ms_per_call=a["idle_kernel_ms"] / calls,
+            ms_per_call_by_kernel={kind_name[k]: a["ms_by_kind"][k] / calls for k in range(3) if a["n_by_kind"][k]},
+            launches_per_call_by_kernel={kind_name[k]: a["n_by_kind"][k] / calls for k in range(3)
+                                         if a["n_by_kind"][k]},
+            pixel_evals_per_call={kind_name[k]: ev[k] / calls for k in range(3) if a["n_by_kind"][k]},
             mpix_iter_per_s=rows * cols * a["k"] * a["calls"] / (a["kernel_ms"] * 1e-3) / 1e6
             if a["kernel_ms"] > 0 else None)
-        if a["kernel_ms"] > dom_ms:
-            dom_b, dom_ms = b, a["kernel_ms"]
-    a = acc[dom_b]
-    taps = (2 * dom_b + 1) ** 2 - 1
-    tests_per_launch = taps * rows * cols * a["passes_executed"] / max(1, a["work_launches"])
-    launch_s = a["kernel_ms"] * 1e-3 / max(1, a["work_launches"])
-    achieved = tests_per_launch / launch_s / 1e9
-    sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
-    alu_peak = sms * 128 * sm_mhz * 1e6 / 1e9
+        for k in range(3):
+            if a["n_by_kind"][k]:
+                kernels.append((a["ms_by_kind"][k], kind_name[k], b, ev[k] * taps, a["n_by_kind"][k], a["T"]))
+    kernels.sort(reverse=True)
+    dom_ms, dom_name, dom_b, dom_tests, dom_n, dom_T = kernels[0]
+    launch_s = dom_ms * 1e-3 / dom_n
+    achieved = dom_tests / dom_n / launch_s / 1e9
+    tname = f"{dom_name}<beta={dom_b},T={dom_T}>" if dom_name == "fused_kernel" else f"{dom_name}<beta={dom_b}>"
     roofline = {
         "bound": "alu",
-        "kernel": f"fused_kernel<beta={dom_b},T={a['T']}>",
+        "kernel": tname,
         "achieved": round(achieved, 1),
         "peak": round(alu_peak, 1),
-        "unit": "Gtest/s",
+        "unit": "Gop/s",
         "frac": round(achieved / alu_peak, 4),
-        "traffic": traffic_from_profiles(dom_b, a["T"], rows, cols),
-        "algorithmic_unit": f"one neighbour comparison of Algorithm 1/2: {taps} per pixel per pass",
+        "traffic": traffic_from_profiles(dom_name, dom_b, dom_T, rows, cols),
+        "algorithmic_unit": (f"one neighbour comparison of Algorithms 1-2 ({(2 * dom_b + 1) ** 2 - 1} per evaluated "
+                             "pixel), counting the pixels a pass must evaluate: every pixel in a dense pass, the "
+                             "pixels within beta of a previous-pass change otherwise"),
         "peak_basis": f"{sms} SMs x 128 lanes x {sm_mhz:.0f} MHz ({peak_kind} sm_max_mhz)",
         "launch_ms": round(launch_s * 1e3, 4),
+        "share_of_step": round(dom_ms / max(1e-9, total_ms), 4),
     }
     pix_iters_per_step = units / max(1, args.steps) / world
     step_s = total_ms * 1e-3 / args.steps
     hbm_eff = 2.0 * pix_iters_per_step / step_s / 1e9
-    launches = sum(acc[b]["launches"] + 3 * acc[b]["calls"] for b in betas)
+    launches = sum(acc[b]["launches"] + 3 * acc[b]["calls"] for b in betas)  # + copy-in, init, copy-out
 
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
@@ -289,7 +304,8 @@ def run_ours(args, rank, world, local):
         "data": "synthetic (seeded Gaussian-bump + gradient content, salt-and-pepper noise)",
         "config": {"workload": w["name"], "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": f"{L2_FLUSH_BYTES >> 20} MiB buffer written before every timed step",
-                   "kernel": "unfused" if args.kernel else "fused", "rows": rows, "cols": cols},
+                   "schedule": {0: "fused tile launch + list passes", 1: "unfused", 2: "fused tile launches"}[
+                       args.kernel], "rows": rows, "cols": cols},
         "roofline": roofline,
         "hbm_effective": {"bytes_per_pixel_iter": 2, "achieved_gbs": round(hbm_eff, 1),
                           "peak_gbs": peaks.get("hbm_gbs"), "frac": round(hbm_eff / peaks.get("hbm_gbs", 6800.0), 4),
@@ -311,11 +327,12 @@ def run_ours(args, rank, world, local):
         print(json.dumps(out), flush=True)
 
 
-def traffic_from_profiles(beta, T, rows, cols):
+def traffic_from_profiles(name, beta, T, rows, cols):
     """DRAM bytes per launch of the dominant kernel from a committed ncu
-    summary (profiles/fused_b{beta}_t{T}.txt, line 'dram_bytes_per_launch:'),
-    or None when no capture of the current kernel exists."""
-    path = os.path.join(ROOT, "profiles", f"fused_b{beta}_t{T}_{rows}x{cols}.txt")
+    summary (profiles/<kernel>_b<beta>[_t<T>]_<rows>x<cols>.txt, line
+    'dram_bytes_per_launch:'), or None when no capture of it exists."""
+    tag = f"{name}_b{beta}" + (f"_t{T}" if name == "fused_kernel" else "")
+    path = os.path.join(ROOT, "profiles", f"{tag}_{rows}x{cols}.txt")
     if not os.path.exists(path):
         return None
     for ln in open(path):

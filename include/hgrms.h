@@ -95,9 +95,13 @@ int hgrms_last_cuda_error(hgrms_t h);
 /* ---- Tuning and measurement (not part of the method) ------------------ */
 
 /* Options for hgrms_set_option. */
-#define HGRMS_OPT_KERNEL   1 /* 0 = fused multi-pass tile kernel (default), 1 = unfused one-pass kernel */
+#define HGRMS_OPT_KERNEL   1 /* 0 = one fused multi-pass tile launch, then one list-pass launch per
+                                 remaining pass (default); 1 = unfused one-pass kernel for every
+                                 pass; 2 = fused tile launches only */
 #define HGRMS_OPT_PASSES   2 /* passes fused per launch; 0 = the built-in choice for beta */
 #define HGRMS_OPT_TIMING   3 /* 1 = time every denoising launch with CUDA events (see hgrms_stats) */
+#define HGRMS_OPT_LIST_CAP 4 /* capacity of the change lists of list passes (0 = rows*cols/4 + 65536);
+                                when a pass changes more pixels, the next pass evaluates every pixel */
 
 /* Set an option.  Returns HGRMS_OK or HGRMS_EINVAL (unknown option or value,
  * e.g. a pass count that has no compiled kernel for some beta is rejected at
@@ -119,9 +123,19 @@ typedef struct hgrms_stats {
                                passes (CUDA events on the handle's stream), else 0 */
     double idle_kernel_ms;  /* HGRMS_OPT_TIMING: summed durations of the launches that found
                                the call already finished and returned at once */
+    long long evals_fused;  /* pixel evaluations the passes needed, fused tile launches
+                               (every image pixel per dense pass, else the pixels within
+                               beta of a change of the previous pass) */
+    long long evals_list;   /* the same for list-pass launches */
 } hgrms_stats_t;
 
 int hgrms_stats(hgrms_t h, hgrms_stats_t* out);
+
+/* Per-launch durations (ms) of the last call, recorded when HGRMS_OPT_TIMING
+ * is on, in launch order; kind[i] (if kind is not NULL) is 0 for a fused tile
+ * launch, 1 for a list pass, 2 for an unfused pass.  Copies at most n entries
+ * and returns the number recorded, or HGRMS_EINVAL. */
+int hgrms_launch_times(hgrms_t h, float* ms, int* kind, int n);
 
 /* The passes per launch the built-in choice uses for beta (1..7), or
  * HGRMS_EINVAL. */

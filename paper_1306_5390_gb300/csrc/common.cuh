@@ -17,31 +17,51 @@ constexpr int kPadY = 16;   // rows above the image (>= any vertical tile halo)
 constexpr int kMaxBeta = 7;
 
 // Iteration state shared by the launches of one denoising call.
+//
+// Three canvases hold images.  `cur` holds the current image I_t.  `aux`
+// holds an image that agrees with I_{t-1} wherever pass t changed nothing
+// (I_{t-1} itself after a one-pass launch); a launch that writes only the
+// pixels that can change (a list pass) writes into `aux`, which then holds
+// I_{t+1} everywhere.
 struct Ctrl {
     unsigned k;          // passes so far that changed at least one pixel
     unsigned converged;  // 1 once a pass changed no pixel
-    unsigned cur;        // canvas holding the current image: 0 = A, 1 = B
+    unsigned cur;        // canvas (0..2) holding the current image
+    unsigned aux;        // canvas (0..2, != cur) partnering it, see above
     unsigned max_k;      // cap on k
     unsigned done;       // CTAs of the running launch that have finished
-    unsigned mask;       // bit t: pass t of the running launch changed a core pixel
+    unsigned mask;       // bit t: pass t of the running launch changed a pixel
     unsigned work_launches;
     unsigned executed;   // passes executed by launches that did work
+    unsigned stamp;      // list-pass claim stamp (monotonic across calls, >= 1)
+    unsigned list_n[2];  // entries appended to change list 0 / 1 (> capacity: overflow)
+    // Pixel evaluations the passes needed (core pixels only: a dense pass
+    // counts every image pixel, a list pass the pixels it claimed), by kernel.
+    unsigned long long evals_fused;
+    unsigned long long evals_list;
 };
 
 struct PassArgs {
-    const uint8_t* canvas_a;  // canvas base pointers (row 0, column 0 of the canvas)
-    uint8_t* canvas_b;
+    uint8_t* canvas[3];       // canvas base pointers (row 0, column 0 of each canvas)
     long long pitch;          // canvas row pitch in bytes (multiple of 16)
     int rows, cols;           // image size
     int alpha;
     int tiles_x;              // tile grid width (fused kernel)
     Ctrl* ctrl;
-    // Pixel change maps (fused kernel): three bitmaps of rows x map_words
-    // 32-bit words; bit (c & 31) of word c >> 5 of row r = image pixel (r, c)
-    // changed in the last pass of a launch.  Launch L writes map L % 3,
-    // reads map (L + 2) % 3 and clears map (L + 1) % 3.
+    // Pixel change maps (fused kernel launched repeatedly): three bitmaps of
+    // rows x map_words 32-bit words; bit (c & 31) of word c >> 5 of row r =
+    // image pixel (r, c) changed in the last pass of a launch.  Launch L
+    // writes map L % 3, reads map (L + 2) % 3 and clears map (L + 1) % 3.
+    // Null when unused.
     uint32_t* chg_maps;
     int map_words;            // words per image row
+    // Change lists (list passes): pixels changed by the last pass of launch
+    // L are appended, packed as (row << 16) | column, to list L & 1; its
+    // length is ctrl->list_n[L & 1].  Null when unused.
+    uint32_t* lists[2];
+    unsigned list_cap;
+    uint32_t* stamps;         // one claim stamp per image pixel (list passes)
+    int write_prev;           // fused kernel: also write I_{t-1} to the third canvas
 };
 
 // Passes the launch must run: 0 when the call has finished.
@@ -55,13 +75,14 @@ __device__ __forceinline__ int launch_passes(const Ctrl* c, int T) {
 }
 
 // Called by thread 0 of every CTA that ran `np` passes.  `cta_mask` bit t is
-// set when pass t changed a pixel of this CTA's core.  The last CTA to arrive
-// folds the launch's mask into the iteration state: k grows by the number of
-// leading changing passes; a pass that changed nothing means the image is a
-// fixed point (every later pass is a no-op, so the buffer written by this
-// launch holds the final image).
-__device__ __forceinline__ void finish_launch(Ctrl* c, unsigned cta_mask, int np,
-                                              unsigned nctas) {
+// set when pass t changed a pixel of this CTA's share of the image.  The last
+// CTA to arrive folds the launch's mask into the iteration state: k grows by
+// the number of leading changing passes; a pass that changed nothing means
+// the image is a fixed point (every later pass is a no-op, so the canvas
+// written by this launch holds the final image).  new_cur / new_aux are the
+// canvases the launch leaves as `cur` and `aux`.
+__device__ __forceinline__ void finish_launch(Ctrl* c, unsigned cta_mask, int np, unsigned nctas,
+                                              unsigned new_cur, unsigned new_aux) {
     if (cta_mask) atomicOr(&c->mask, cta_mask);
     __threadfence();
     unsigned prev = atomicAdd(&c->done, 1u);
@@ -72,12 +93,30 @@ __device__ __forceinline__ void finish_launch(Ctrl* c, unsigned cta_mask, int np
         if (ones > (unsigned)np) ones = (unsigned)np;
         c->k += ones;
         if (ones < (unsigned)np) c->converged = 1u;
-        c->cur ^= 1u;
-        c->work_launches += 1u;
+        c->cur = new_cur;
+        c->aux = new_aux;
+        const unsigned L = c->work_launches;
+        // The next launch appends to list (L + 1) & 1, which this launch read.
+        c->list_n[(L + 1u) & 1u] = 0u;
+        c->work_launches = L + 1u;
         c->executed += (unsigned)np;
+        c->stamp += 1u;
         c->done = 0u;
         __threadfence();
     }
+}
+
+// Warp-aggregated append of this lane's value (when `want`) to a global list.
+// Every lane of the warp must call it.
+__device__ __forceinline__ void list_append(uint32_t* list, unsigned* n, unsigned cap, bool want, uint32_t v,
+                                            int lane) {
+    const unsigned bal = __ballot_sync(0xffffffffu, want);
+    if (!bal) return;
+    const int leader = __ffs(bal) - 1;
+    unsigned pos = 0;
+    if (lane == leader) pos = atomicAdd(n, (unsigned)__popc(bal));
+    pos = __shfl_sync(0xffffffffu, pos, leader) + (unsigned)__popc(bal & ((1u << lane) - 1u));
+    if (want && pos < cap) list[pos] = v;
 }
 
 }  // namespace hg

@@ -230,6 +230,7 @@ struct PassCtx {
     int ncand;           // entries in the list (warp-uniform)
     uint16_t* list;      // changed pixels of this pass (index y * SW + x)
     int* nlist;          // its counter (may exceed kListCap: overflow)
+    unsigned evals;      // core pixels this thread evaluated in list passes
     int x0, y0, rows, cols, alpha;
     bool changed_core;   // this lane saw a core pixel change
 };
@@ -377,6 +378,7 @@ __device__ __forceinline__ void list_pass(PassCtx<B, T>& c, const uint16_t* prev
         const int q = y * G::SW + x;
         const uint32_t bit = 1u << (q & 31);
         if (atomicOr(&mark[q >> 5], bit) & bit) continue;  // someone else evaluates q
+        if (in_core_px(y, x, G::H, G::TH, G::TW)) ++c.evals;
         const __half old = hin[q];
         __half nv = old;
         const int gx = c.x0 + x - kPadX, gy = c.y0 + y - G::H;
@@ -399,20 +401,22 @@ fused_kernel(PassArgs a) {
     using G = FusedGeo<B, T>;
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int s_np;
-    __shared__ unsigned s_cur, s_launch;
+    __shared__ unsigned s_cur, s_aux, s_launch;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
         s_np = launch_passes(a.ctrl, T);
         s_cur = __ldcg(&a.ctrl->cur);
+        s_aux = __ldcg(&a.ctrl->aux);
         s_launch = __ldcg(&a.ctrl->work_launches);
     }
     __syncthreads();
     const int np = s_np;
     if (np == 0) return;
     const unsigned L = s_launch;
-    const uint8_t* src = s_cur ? a.canvas_b : a.canvas_a;
-    uint8_t* dst = s_cur ? const_cast<uint8_t*>(a.canvas_a) : a.canvas_b;
+    const unsigned cur = s_cur, aux = s_aux, third = 3u - s_cur - s_aux;
+    const uint8_t* src = a.canvas[cur];
+    uint8_t* dst = a.canvas[aux];
     const int tx = blockIdx.x % a.tiles_x;
     const int ty = blockIdx.x / a.tiles_x;
     const int x0 = tx * G::TW, y0 = ty * G::TH;
@@ -422,10 +426,11 @@ fused_kernel(PassArgs a) {
     uint16_t* lists = reinterpret_cast<uint16_t*>(smem + G::kListOff);  // 2 lists: pass t uses t & 1
     uint32_t* marks = reinterpret_cast<uint32_t*>(smem + G::kMarkOff);  // 2 bitmaps: pass t uses t & 1
     int* s_cnt = reinterpret_cast<int*>(smem + G::kCntOff);             // list counters, pass t uses t % 3
-    const size_t map_size = (size_t)a.rows * (size_t)a.map_words;
-    uint32_t* map_out = a.chg_maps + (size_t)(L % 3u) * map_size;
-    const uint32_t* map_in = a.chg_maps + (size_t)((L + 2u) % 3u) * map_size;
-    uint32_t* map_clr = a.chg_maps + (size_t)((L + 1u) % 3u) * map_size;
+    const bool use_maps = a.chg_maps != nullptr;
+    const size_t map_size = use_maps ? (size_t)a.rows * (size_t)a.map_words : 0;
+    uint32_t* map_out = use_maps ? a.chg_maps + (size_t)(L % 3u) * map_size : nullptr;
+    const uint32_t* map_in = use_maps ? a.chg_maps + (size_t)((L + 2u) % 3u) * map_size : nullptr;
+    uint32_t* map_clr = use_maps ? a.chg_maps + (size_t)((L + 1u) % 3u) * map_size : nullptr;
 
     // Tile with halo: image rows [y0 - H, y0 + TH + H), columns [x0 - 16,
     // x0 + TW + 16); always inside the canvas.  Bytes -> fp16 pairs, into
@@ -453,12 +458,13 @@ fused_kernel(PassArgs a) {
         if (tid < 4) s_cnt[tid] = 0;
         // Clear this CTA's share of the map the next launch writes.
         for (size_t i = (size_t)blockIdx.x * G::kThreads + tid; i < map_size; i += (size_t)gridDim.x * G::kThreads)
-            map_clr[i] = 0u;
+            map_clr[i] = 0u;  // map_size is 0 without maps
     }
     __syncthreads();
     // Pass 0's "previous pass": the pixels the previous launch's last pass
     // changed (global map), listed in list 1 / counter 2.
-    if (L > 0) {
+    const bool from_map = use_maps && L > 0;
+    if (from_map) {
         const int wlo = (x0 - kPadX) >> 5;  // floor division (x0 - 16 >= -16)
         const int nw = ((x0 + G::TW + kPadX - 1) >> 5) - wlo + 1;
         for (int i = tid; i < G::SH * nw; i += G::kThreads) {
@@ -490,6 +496,8 @@ fused_kernel(PassArgs a) {
     c.rows = a.rows;
     c.cols = a.cols;
     c.alpha = a.alpha;
+    c.evals = 0;
+    int dense_passes = 0;
     for (int t = 0; t < np; ++t) {
         c.in = (t & 1) ? buf1 : buf0;
         c.out = (t & 1) ? buf0 : buf1;
@@ -503,8 +511,9 @@ fused_kernel(PassArgs a) {
         if (tid == 0) s_cnt[(t + 1) % 3] = 0;
         uint32_t* mark_next = marks + ((t + 1) & 1) * G::kMarkWords;
         for (int i = tid; i < G::kMarkWords; i += G::kThreads) mark_next[i] = 0u;
-        const bool dense = (t == 0 && L == 0) || nprev > G::kListCap || nprev * G::P > G::kListEvalMax;
+        const bool dense = (t == 0 && !from_map) || nprev > G::kListCap || nprev * G::P > G::kListEvalMax;
         if (dense) {
+            ++dense_passes;
             band_dense<B, T>(c, ys, ws, lane, two_a);
             flush_candidates<B, T>(c, lane);
         } else {
@@ -512,15 +521,19 @@ fused_kernel(PassArgs a) {
         }
         if (__syncthreads_or(c.changed_core)) cta_mask |= 1u << t;
     }
-    const uint32_t* fin = (np & 1) ? buf1 : buf0;
+    const uint32_t* fin = (np & 1) ? buf1 : buf0;  // I_np
+    const uint32_t* pen = (np & 1) ? buf0 : buf1;  // I_(np-1) (the loaded tile when np == 1)
 
-    // Core -> canvas bytes.
+    // Core -> canvas bytes (and I_(np-1) -> the third canvas when asked).
     {
-        uint8_t* base = dst + (long long)(kPadY + y0) * a.pitch + kPadX + x0;
+        const long long off = (long long)(kPadY + y0) * a.pitch + kPadX + x0;
+        uint8_t* base = dst + off;
+        uint8_t* base_prev = a.canvas[third] + off;
         constexpr int CH = G::TW / 16;
         for (int i = tid; i < G::TH * CH; i += G::kThreads) {
             const int r = i / CH, cc = i - r * CH;
-            const uint4* s = reinterpret_cast<const uint4*>(fin + (G::H + r) * G::SWW + kPadX / 2 + cc * 8);
+            const int so = (G::H + r) * G::SWW + kPadX / 2 + cc * 8;
+            const uint4* s = reinterpret_cast<const uint4*>(fin + so);
             const uint4 p = s[0], q = s[1];
             uint4 o;
             o.x = h2_to_bytes(p.x, p.y);
@@ -528,13 +541,48 @@ fused_kernel(PassArgs a) {
             o.z = h2_to_bytes(q.x, q.y);
             o.w = h2_to_bytes(q.z, q.w);
             *reinterpret_cast<uint4*>(base + (long long)r * a.pitch + cc * 16) = o;
+            if (a.write_prev) {
+                const uint4* s2 = reinterpret_cast<const uint4*>(pen + so);
+                const uint4 p2 = s2[0], q2 = s2[1];
+                o.x = h2_to_bytes(p2.x, p2.y);
+                o.y = h2_to_bytes(p2.z, p2.w);
+                o.z = h2_to_bytes(q2.x, q2.y);
+                o.w = h2_to_bytes(q2.z, q2.w);
+                *reinterpret_cast<uint4*>(base_prev + (long long)r * a.pitch + cc * 16) = o;
+            }
+        }
+    }
+    const int nlast = s_cnt[(np - 1) % 3];
+    const uint16_t* last = lists + ((np - 1) & 1) * G::kListCap;
+    // The last pass's changed core pixels -> the global change list that the
+    // next (list) pass starts from; an overflowed tile list forces that pass
+    // to be dense.
+    if (a.lists[0] != nullptr) {
+        uint32_t* glist = a.lists[L & 1u];
+        unsigned* gn = &a.ctrl->list_n[L & 1u];
+        if (nlast <= G::kListCap) {
+            for (int base = warp * 32; base < nlast; base += G::kThreads) {
+                const int i = base + lane;
+                bool want = false;
+                uint32_t v = 0;
+                if (i < nlast) {
+                    const int q = last[i];
+                    const int y = q / G::SW, x = q - y * G::SW;
+                    const int gy = y0 + y - G::H, gx = x0 + x - kPadX;
+                    if (in_core_px(y, x, G::H, G::TH, G::TW) && gy < a.rows && gx < a.cols) {
+                        want = true;
+                        v = ((uint32_t)gy << 16) | (uint32_t)gx;
+                    }
+                }
+                list_append(glist, gn, a.list_cap, want, v, lane);
+            }
+        } else if (tid == 0) {
+            atomicAdd(gn, a.list_cap + 1u);
         }
     }
     // The last pass's changed core pixels -> this launch's map (all core
     // pixels when the list overflowed: a superset is always safe).
-    {
-        const int nlast = s_cnt[(np - 1) % 3];
-        const uint16_t* last = lists + ((np - 1) & 1) * G::kListCap;
+    if (use_maps) {
         if (nlast <= G::kListCap) {
             for (int i = tid; i < nlast; i += G::kThreads) {
                 const int q = last[i];
@@ -557,7 +605,16 @@ fused_kernel(PassArgs a) {
             }
         }
     }
-    if (tid == 0) finish_launch(a.ctrl, cta_mask, np, gridDim.x);
+    // Work accounting: dense passes evaluate every core pixel on the image.
+    {
+        unsigned long long ev = __reduce_add_sync(0xffffffffu, c.evals);
+        if (tid == 0) {
+            const int ch = min(G::TH, a.rows - y0), cw = min(G::TW, a.cols - x0);
+            ev += (unsigned long long)dense_passes * (unsigned long long)(ch * cw);
+        }
+        if (lane == 0 && ev) atomicAdd(&a.ctrl->evals_fused, ev);
+    }
+    if (tid == 0) finish_launch(a.ctrl, cta_mask, np, gridDim.x, aux, a.write_prev ? third : cur);
 }
 
 // Host-side description of one compiled (beta, T) instance.

@@ -19,7 +19,8 @@ cudaError_t launch_plain(int beta, const PassArgs& a, cudaStream_t s);
 cudaError_t launch_ctrl_init(Ctrl* c, unsigned max_k, cudaStream_t s);
 cudaError_t launch_copy_in(const uint8_t* img, int rows, int cols, uint8_t* canvas, long long pitch,
                            int sms, cudaStream_t s);
-cudaError_t launch_copy_out(const Ctrl* c, const uint8_t* ca, const uint8_t* cb, long long pitch,
-                            uint8_t* img, int rows, int cols, int sms, cudaStream_t s);
+cudaError_t launch_copy_out(const Ctrl* c, uint8_t* const canvas[3], long long pitch, uint8_t* img, int rows,
+                            int cols, int sms, cudaStream_t s);
+cudaError_t launch_list(int beta, const PassArgs& a, int sms, cudaStream_t s);
 
 }  // namespace hg

@@ -15,16 +15,17 @@ namespace hg {
 template <int B>
 __global__ void __launch_bounds__(256) plain_kernel(PassArgs a) {
     __shared__ int s_np;
-    __shared__ unsigned s_cur;
+    __shared__ unsigned s_cur, s_aux;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
     if (tid == 0) {
         s_np = launch_passes(a.ctrl, 1);
         s_cur = __ldcg(&a.ctrl->cur);
+        s_aux = __ldcg(&a.ctrl->aux);
     }
     __syncthreads();
     if (s_np == 0) return;
-    const uint8_t* src = s_cur ? a.canvas_b : a.canvas_a;
-    uint8_t* dst = s_cur ? const_cast<uint8_t*>(a.canvas_a) : a.canvas_b;
+    const uint8_t* src = a.canvas[s_cur];
+    uint8_t* dst = a.canvas[s_aux];
     const int x = blockIdx.x * blockDim.x + threadIdx.x;
     const int y = blockIdx.y * blockDim.y + threadIdx.y;
     bool changed = false;
@@ -63,7 +64,7 @@ __global__ void __launch_bounds__(256) plain_kernel(PassArgs a) {
         changed = outv != ip;
     }
     const int any = __syncthreads_or(changed);
-    if (tid == 0) finish_launch(a.ctrl, any ? 1u : 0u, 1, gridDim.x * gridDim.y);
+    if (tid == 0) finish_launch(a.ctrl, any ? 1u : 0u, 1, gridDim.x * gridDim.y, s_aux, s_cur);
 }
 
 cudaError_t launch_plain(int beta, const PassArgs& a, cudaStream_t s) {
@@ -86,11 +87,17 @@ __global__ void ctrl_init_kernel(Ctrl* c, unsigned max_k) {
     c->k = 0;
     c->converged = 0;
     c->cur = 0;
+    c->aux = 1;
     c->max_k = max_k;
     c->done = 0;
     c->mask = 0;
     c->work_launches = 0;
     c->executed = 0;
+    if (c->stamp == 0) c->stamp = 1;  // stamps are never reset; 0 means "never claimed"
+    c->list_n[0] = 0;
+    c->list_n[1] = 0;
+    c->evals_fused = 0;
+    c->evals_list = 0;
 }
 
 cudaError_t launch_ctrl_init(Ctrl* c, unsigned max_k, cudaStream_t s) {
@@ -119,10 +126,11 @@ __global__ void copy_in_kernel(const uint8_t* __restrict__ img, int rows, int co
     }
 }
 
-__global__ void copy_out_kernel(const Ctrl* __restrict__ c, const uint8_t* __restrict__ ca,
-                                const uint8_t* __restrict__ cb, long long pitch,
+__global__ void copy_out_kernel(const Ctrl* __restrict__ c, const uint8_t* __restrict__ c0,
+                                const uint8_t* __restrict__ c1, const uint8_t* __restrict__ c2, long long pitch,
                                 uint8_t* __restrict__ img, int rows, int cols, int vec) {
-    const uint8_t* canvas = __ldcg(&c->cur) ? cb : ca;
+    const unsigned cur = __ldcg(&c->cur);
+    const uint8_t* canvas = cur == 0 ? c0 : (cur == 1 ? c1 : c2);
     const long long chunks = (cols + 15) / 16;
     const long long total = chunks * rows;
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
@@ -156,10 +164,11 @@ cudaError_t launch_copy_in(const uint8_t* img, int rows, int cols, uint8_t* canv
     return cudaGetLastError();
 }
 
-cudaError_t launch_copy_out(const Ctrl* c, const uint8_t* ca, const uint8_t* cb, long long pitch,
-                            uint8_t* img, int rows, int cols, int sms, cudaStream_t s) {
+cudaError_t launch_copy_out(const Ctrl* c, uint8_t* const canvas[3], long long pitch, uint8_t* img, int rows,
+                            int cols, int sms, cudaStream_t s) {
     const int vec = (cols % 16 == 0) && ((reinterpret_cast<uintptr_t>(img) & 15u) == 0);
-    copy_out_kernel<<<copy_grid(rows, cols, sms), 256, 0, s>>>(c, ca, cb, pitch, img, rows, cols, vec);
+    copy_out_kernel<<<copy_grid(rows, cols, sms), 256, 0, s>>>(c, canvas[0], canvas[1], canvas[2], pitch, img,
+                                                               rows, cols, vec);
     return cudaGetLastError();
 }
 

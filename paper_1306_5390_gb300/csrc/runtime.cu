@@ -3,10 +3,13 @@
 // One call of hgrms_denoise:
 //   1. copy the image into canvas A (padded, 16-byte aligned rows),
 //   2. reset the device control block (k = 0, current canvas = A),
-//   3. enqueue ceil(max_k / T) fused launches; each runs up to T passes
-//      (Section 2's iteration) and the last CTA of each launch updates k,
-//      the converged flag and the current canvas on the device, so no launch
-//      waits for the host; launches after the end return at once,
+//   3. enqueue the passes (Section 2's iteration): by default one fused
+//      launch of T passes on shared-memory tiles (the passes where many
+//      pixels change), then one list-pass launch per remaining pass, which
+//      evaluates only the windows around the pixels the previous pass
+//      changed.  The last CTA of each launch updates k, the converged flag
+//      and the current canvas on the device, so no launch waits for the
+//      host; launches after the end return at once,
 //   4. copy the current canvas back and read k with one device-to-host copy.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -25,10 +28,14 @@ struct hgrms_ctx {
     int device = 0;
     int sms = 0;
     cudaStream_t stream = nullptr;
-    uint8_t* canvas[2] = {nullptr, nullptr};
+    uint8_t* canvas[3] = {nullptr, nullptr, nullptr};
     size_t canvas_bytes = 0;
-    uint32_t* chg_maps = nullptr;  // three pixel change bitmaps (fused kernel)
+    uint32_t* chg_maps = nullptr;  // three pixel change bitmaps (repeated fused launches)
     size_t chg_map_bytes = 0;
+    uint32_t* lists = nullptr;     // two change lists (list passes)
+    size_t list_cap = 0;
+    uint32_t* stamps = nullptr;    // per-pixel claim stamps (list passes)
+    size_t stamp_count = 0;
     hg::Ctrl* ctrl = nullptr;
     hg::Ctrl* host_ctrl = nullptr;
     int last_cuda_error = 0;
@@ -36,8 +43,11 @@ struct hgrms_ctx {
     int opt_kernel = 0;
     int opt_passes = 0;
     int opt_timing = 0;
+    int opt_list_cap = 0;
     hgrms_stats_t stats{};
     std::vector<cudaEvent_t> events;
+    std::vector<float> launch_ms;  // per-launch durations of the last call (HGRMS_OPT_TIMING)
+    std::vector<int> launch_kind;  // 0 = fused, 1 = list pass, 2 = unfused
 };
 
 namespace {
@@ -107,20 +117,27 @@ int pointer_kind(const void* p, int device) {
     return 0;
 }
 
+enum Schedule { kHybrid = 0, kPlain = 1, kFusedOnly = 2 };
+
 struct Plan {
+    int schedule;
     bool fused;
     const hg::FusedEntry* fe;
     int T;
     int tiles_x, tiles_y;
     long long pitch;
     long long crows;
-    int launches;
+    int launches;       // all launches
+    int fused_launches; // of which fused
     int map_words;
+    size_t list_cap;
 };
 
 int make_plan(hgrms_ctx* h, int rows, int cols, int beta, int max_k, Plan* p) {
-    p->fused = h->opt_kernel == 0;
+    p->schedule = h->opt_kernel;
+    p->fused = p->schedule != kPlain;
     p->fe = nullptr;
+    p->list_cap = 0;
     if (p->fused) {
         p->T = h->opt_passes > 0 ? h->opt_passes : default_passes(beta);
         p->fe = find_fused(beta, p->T);
@@ -130,8 +147,16 @@ int make_plan(hgrms_ctx* h, int rows, int cols, int beta, int max_k, Plan* p) {
         const long long need_w = hg::kPadX + (long long)p->tiles_x * p->fe->TW + 16;
         p->pitch = (need_w + 127) / 128 * 128;
         p->crows = hg::kPadY + (long long)p->tiles_y * p->fe->TH + 16;
-        p->launches = (max_k + p->T - 1) / p->T;
-        p->map_words = (p->tiles_x * p->fe->TW + 31) / 32 + 2;
+        if (p->schedule == kHybrid) {
+            p->fused_launches = max_k > 0 ? 1 : 0;
+            p->launches = max_k > p->T ? 1 + (max_k - p->T) : p->fused_launches;
+            p->map_words = 0;
+            p->list_cap = h->opt_list_cap > 0 ? (size_t)h->opt_list_cap
+                                              : (size_t)rows * (size_t)cols / 4 + 65536;
+        } else {
+            p->fused_launches = p->launches = (max_k + p->T - 1) / p->T;
+            p->map_words = (p->tiles_x * p->fe->TW + 31) / 32 + 2;
+        }
     } else {
         p->T = 1;
         p->tiles_x = p->tiles_y = 0;
@@ -139,6 +164,7 @@ int make_plan(hgrms_ctx* h, int rows, int cols, int beta, int max_k, Plan* p) {
         p->pitch = (need_w + 127) / 128 * 128;
         p->crows = hg::kPadY + (long long)rows + 16;
         p->launches = max_k;
+        p->fused_launches = 0;
         p->map_words = 0;
     }
     return HGRMS_OK;
@@ -146,12 +172,12 @@ int make_plan(hgrms_ctx* h, int rows, int cols, int beta, int max_k, Plan* p) {
 
 int ensure_canvas(hgrms_ctx* h, size_t bytes) {
     if (bytes <= h->canvas_bytes) return HGRMS_OK;
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 3; ++i) {
         if (h->canvas[i]) cudaFree(h->canvas[i]);
         h->canvas[i] = nullptr;
     }
     h->canvas_bytes = 0;
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < 3; ++i) {
         HG_TRY(h, cudaMalloc(&h->canvas[i], bytes));
         HG_TRY(h, cudaMemsetAsync(h->canvas[i], 0, bytes, h->stream));
     }
@@ -166,6 +192,25 @@ int ensure_maps(hgrms_ctx* h, size_t bytes) {
     h->chg_map_bytes = 0;
     HG_TRY(h, cudaMalloc(&h->chg_maps, bytes));
     h->chg_map_bytes = bytes;
+    return HGRMS_OK;
+}
+
+int ensure_lists(hgrms_ctx* h, size_t cap, size_t pixels) {
+    if (cap > h->list_cap) {
+        if (h->lists) cudaFree(h->lists);
+        h->lists = nullptr;
+        h->list_cap = 0;
+        HG_TRY(h, cudaMalloc(&h->lists, 2 * cap * sizeof(uint32_t)));
+        h->list_cap = cap;
+    }
+    if (pixels > h->stamp_count) {
+        if (h->stamps) cudaFree(h->stamps);
+        h->stamps = nullptr;
+        h->stamp_count = 0;
+        HG_TRY(h, cudaMalloc(&h->stamps, pixels * sizeof(uint32_t)));
+        HG_TRY(h, cudaMemsetAsync(h->stamps, 0, pixels * sizeof(uint32_t), h->stream));
+        h->stamp_count = pixels;
+    }
     return HGRMS_OK;
 }
 
@@ -188,13 +233,16 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     rc = ensure_canvas(h, (size_t)(p.pitch * p.crows));
     if (rc < 0) return rc;
     const size_t map_bytes = (size_t)rows * (size_t)p.map_words * sizeof(uint32_t);
-    if (p.fused) {
+    if (p.map_words > 0) {
         rc = ensure_maps(h, 3 * map_bytes);
+        if (rc < 0) return rc;
+    }
+    if (p.list_cap > 0) {
+        rc = ensure_lists(h, p.list_cap, (size_t)rows * (size_t)cols);
         if (rc < 0) return rc;
     }
     cudaStream_t s = h->stream;
     uint8_t* ca = h->canvas[0];
-    uint8_t* cb = h->canvas[1];
     if (dev) {
         HG_TRY(h, hg::launch_copy_in(img, rows, cols, ca, p.pitch, h->sms, s));
     } else {
@@ -203,18 +251,22 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     }
     HG_TRY(h, hg::launch_ctrl_init(h->ctrl, (unsigned)max_k, s));
     // Map 0 is written by the first launch; the launches clear the others.
-    if (p.fused) HG_TRY(h, cudaMemsetAsync(h->chg_maps, 0, map_bytes, s));
+    if (p.map_words > 0) HG_TRY(h, cudaMemsetAsync(h->chg_maps, 0, map_bytes, s));
     hg::PassArgs a;
-    a.canvas_a = ca;
-    a.canvas_b = cb;
+    for (int i = 0; i < 3; ++i) a.canvas[i] = h->canvas[i];
     a.pitch = p.pitch;
     a.rows = rows;
     a.cols = cols;
     a.alpha = alpha;
     a.tiles_x = p.tiles_x;
     a.ctrl = h->ctrl;
-    a.chg_maps = h->chg_maps;
+    a.chg_maps = p.map_words > 0 ? h->chg_maps : nullptr;
     a.map_words = p.map_words;
+    a.lists[0] = p.list_cap > 0 ? h->lists : nullptr;
+    a.lists[1] = p.list_cap > 0 ? h->lists + p.list_cap : nullptr;
+    a.list_cap = (unsigned)p.list_cap;
+    a.stamps = h->stamps;
+    a.write_prev = p.schedule == kHybrid ? 1 : 0;
     // Per-launch timing is limited to calls of at most kMaxTimedLaunches launches.
     constexpr int kMaxTimedLaunches = 4096;
     const bool timed = h->opt_timing && p.launches <= kMaxTimedLaunches;
@@ -224,13 +276,15 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     }
     for (int i = 0; i < p.launches; ++i) {
         if (timed) HG_TRY(h, cudaEventRecord(h->events[2 * i], s));
-        if (p.fused)
+        if (i < p.fused_launches)
             HG_TRY(h, p.fe->launch(a, p.tiles_y, s));
+        else if (p.fused)
+            HG_TRY(h, hg::launch_list(beta, a, h->sms, s));
         else
             HG_TRY(h, hg::launch_plain(beta, a, s));
         if (timed) HG_TRY(h, cudaEventRecord(h->events[2 * i + 1], s));
     }
-    if (dev) HG_TRY(h, hg::launch_copy_out(h->ctrl, ca, cb, p.pitch, img, rows, cols, h->sms, s));
+    if (dev) HG_TRY(h, hg::launch_copy_out(h->ctrl, h->canvas, p.pitch, img, rows, cols, h->sms, s));
     h->stats.launches += p.launches;
     h->stats.passes_per_launch = p.T;
     h->stats.tile_rows = p.fused ? p.fe->TH : 0;
@@ -242,7 +296,7 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     HG_TRY(h, cudaStreamSynchronize(s));
     const hg::Ctrl c = *h->host_ctrl;
     if (!dev) {
-        const uint8_t* fin = c.cur ? cb : ca;
+        const uint8_t* fin = h->canvas[c.cur];
         HG_TRY(h, cudaMemcpy2DAsync(img, (size_t)cols, fin + hg::kPadY * p.pitch + hg::kPadX, (size_t)p.pitch,
                                     (size_t)cols, (size_t)rows, cudaMemcpyDeviceToHost, s));
         HG_TRY(h, cudaStreamSynchronize(s));
@@ -253,6 +307,8 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
         for (int i = 0; i < p.launches; ++i) {
             float ms = 0.f;
             HG_TRY(h, cudaEventElapsedTime(&ms, h->events[2 * i], h->events[2 * i + 1]));
+            h->launch_ms.push_back(ms);
+            h->launch_kind.push_back(i < p.fused_launches ? 0 : (p.fused ? 1 : 2));
             if (i < (int)c.work_launches)
                 h->stats.kernel_ms += ms;
             else
@@ -260,6 +316,8 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
         }
     }
     h->stats.passes_executed += (int)c.executed;
+    h->stats.evals_fused += (long long)c.evals_fused;
+    h->stats.evals_list += (long long)c.evals_list;
     h->stats.work_launches += (int)c.work_launches;
     h->stats.passes += (int)(c.k + c.converged);
     h->converged = (int)c.converged;
@@ -285,6 +343,7 @@ HG_EXPORT int hgrms_create(hgrms_t* out, int device, void* cuda_stream) {
     int rc = HGRMS_OK;
     cudaError_t e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaMalloc(&h->ctrl, sizeof(hg::Ctrl));
+    if (e == cudaSuccess) e = cudaMemset(h->ctrl, 0, sizeof(hg::Ctrl));
     if (e == cudaSuccess) e = cudaMallocHost(&h->host_ctrl, sizeof(hg::Ctrl));
     if (e != cudaSuccess) {
         rc = cuda_fail(h, e);
@@ -300,10 +359,12 @@ HG_EXPORT void hgrms_destroy(hgrms_t h) {
     {
         DeviceGuard g(h->device);
         if (h->stream) cudaStreamSynchronize(h->stream);
-        for (int i = 0; i < 2; ++i)
+        for (int i = 0; i < 3; ++i)
             if (h->canvas[i]) cudaFree(h->canvas[i]);
         if (h->ctrl) cudaFree(h->ctrl);
         if (h->chg_maps) cudaFree(h->chg_maps);
+        if (h->lists) cudaFree(h->lists);
+        if (h->stamps) cudaFree(h->stamps);
         if (h->host_ctrl) cudaFreeHost(h->host_ctrl);
         for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     }
@@ -318,6 +379,8 @@ HG_EXPORT int hgrms_denoise(hgrms_t h, uint8_t* img, int rows, int cols, int alp
     const int kind = pointer_kind(img, h->device);
     if (kind < 0) return HGRMS_EINVAL;
     h->stats = hgrms_stats_t{};
+    h->launch_ms.clear();
+    h->launch_kind.clear();
     return denoise_one(h, img, rows, cols, alpha, beta, max_k, kind == 1, true);
 }
 
@@ -337,6 +400,8 @@ HG_EXPORT int hgrms_denoise_batch(hgrms_t h, uint8_t* const* imgs, const int* ro
     }
     hgrms_stats_t acc{};
     int all_conv = 1;
+    h->launch_ms.clear();
+    h->launch_kind.clear();
     for (int i = 0; i < n; ++i) {
         h->stats = hgrms_stats_t{};
         const int k = denoise_one(h, imgs[i], rows[i], cols[i], alpha, beta, max_k, kind0 == 1, true);
@@ -349,6 +414,8 @@ HG_EXPORT int hgrms_denoise_batch(hgrms_t h, uint8_t* const* imgs, const int* ro
         acc.kernel_ms += h->stats.kernel_ms;
         acc.idle_kernel_ms += h->stats.idle_kernel_ms;
         acc.passes_executed += h->stats.passes_executed;
+        acc.evals_fused += h->stats.evals_fused;
+        acc.evals_list += h->stats.evals_list;
         acc.passes_per_launch = h->stats.passes_per_launch;
         acc.tile_rows = h->stats.tile_rows;
         acc.tile_cols = h->stats.tile_cols;
@@ -385,7 +452,7 @@ HG_EXPORT int hgrms_set_option(hgrms_t h, int option, int value) {
     if (!h) return HGRMS_EINVAL;
     switch (option) {
         case HGRMS_OPT_KERNEL:
-            if (value != 0 && value != 1) return HGRMS_EINVAL;
+            if (value < 0 || value > 2) return HGRMS_EINVAL;
             h->opt_kernel = value;
             return HGRMS_OK;
         case HGRMS_OPT_PASSES:
@@ -396,6 +463,10 @@ HG_EXPORT int hgrms_set_option(hgrms_t h, int option, int value) {
             if (value != 0 && value != 1) return HGRMS_EINVAL;
             h->opt_timing = value;
             return HGRMS_OK;
+        case HGRMS_OPT_LIST_CAP:
+            if (value < 0) return HGRMS_EINVAL;
+            h->opt_list_cap = value;
+            return HGRMS_OK;
         default: return HGRMS_EINVAL;
     }
 }
@@ -404,6 +475,16 @@ HG_EXPORT int hgrms_stats(hgrms_t h, hgrms_stats_t* out) {
     if (!h || !out) return HGRMS_EINVAL;
     *out = h->stats;
     return HGRMS_OK;
+}
+
+HG_EXPORT int hgrms_launch_times(hgrms_t h, float* ms, int* kind, int n) {
+    if (!h || n < 0 || (n > 0 && !ms)) return HGRMS_EINVAL;
+    const int m = (int)h->launch_ms.size();
+    for (int i = 0; i < n && i < m; ++i) {
+        ms[i] = h->launch_ms[i];
+        if (kind) kind[i] = h->launch_kind[i];
+    }
+    return m;
 }
 
 HG_EXPORT int hgrms_default_passes(int beta) {

@@ -27,12 +27,13 @@ HGRMS_ENODEV = -5
 HGRMS_OPT_KERNEL = 1
 HGRMS_OPT_PASSES = 2
 HGRMS_OPT_TIMING = 3
+HGRMS_OPT_LIST_CAP = 4
 
 # Every symbol the header declares (the CPU tests check the library exports them).
 EXPORTED = (
     "hgrms_create", "hgrms_destroy", "hgrms_denoise", "hgrms_denoise_batch",
     "hgrms_converged", "hgrms_strerror", "hgrms_last_cuda_error", "hgrms_set_option",
-    "hgrms_stats", "hgrms_default_passes", "hgrms_has_kernel",
+    "hgrms_stats", "hgrms_launch_times", "hgrms_default_passes", "hgrms_has_kernel",
 )
 
 
@@ -48,6 +49,8 @@ class hgrms_stats_t(ctypes.Structure):
         ("ctas_per_launch", ctypes.c_longlong),
         ("kernel_ms", ctypes.c_double),
         ("idle_kernel_ms", ctypes.c_double),
+        ("evals_fused", ctypes.c_longlong),
+        ("evals_list", ctypes.c_longlong),
     ]
 
     def as_dict(self):
@@ -96,6 +99,8 @@ def load_library(path: str | None = None):
         lib.hgrms_set_option.restype = ctypes.c_int
         lib.hgrms_stats.argtypes = [vp, ctypes.POINTER(hgrms_stats_t)]
         lib.hgrms_stats.restype = ctypes.c_int
+        lib.hgrms_launch_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ip, ctypes.c_int]
+        lib.hgrms_launch_times.restype = ctypes.c_int
         lib.hgrms_default_passes.argtypes = [ctypes.c_int]
         lib.hgrms_default_passes.restype = ctypes.c_int
         lib.hgrms_has_kernel.argtypes = [ctypes.c_int, ctypes.c_int]
@@ -160,6 +165,18 @@ def hgrms_stats(h) -> dict:
     if rc != HGRMS_OK:
         raise HgrmsError(rc, "hgrms_stats")
     return st.as_dict()
+
+
+def hgrms_launch_times(h):
+    """[(ms, kind)] per launch of the last call (kind 0 fused, 1 list, 2 unfused)."""
+    lib = load_library()
+    n = lib.hgrms_launch_times(h, None, None, 0)
+    if n < 0:
+        raise HgrmsError(n, "hgrms_launch_times")
+    ms = (ctypes.c_float * max(n, 1))()
+    kd = (ctypes.c_int * max(n, 1))()
+    lib.hgrms_launch_times(h, ms, kd, n)
+    return [(float(ms[i]), int(kd[i])) for i in range(n)]
 
 
 def hgrms_default_passes(beta: int) -> int:
@@ -238,6 +255,9 @@ class Denoiser:
 
     def stats(self) -> dict:
         return hgrms_stats(self.h)
+
+    def launch_times(self):
+        return hgrms_launch_times(self.h)
 
 
 def denoise(img, alpha: int, beta: int, max_k: int, device: int = 0) -> int:

@@ -36,10 +36,11 @@ def den(torch_cuda):
     d.close()
 
 
-def gpu_denoise(d, torch, img, alpha, beta, max_k, passes=0, kernel=0, host=False):
+def gpu_denoise(d, torch, img, alpha, beta, max_k, passes=0, kernel=0, host=False, list_cap=0):
     from paper_1306_5390_gb300 import hgrms
     d.set_option(hgrms.HGRMS_OPT_PASSES, passes)
     d.set_option(hgrms.HGRMS_OPT_KERNEL, kernel)
+    d.set_option(hgrms.HGRMS_OPT_LIST_CAP, list_cap)
     if host:
         out = np.ascontiguousarray(img).copy()
         k = d.denoise(out, alpha, beta, max_k)
@@ -103,6 +104,25 @@ def test_max_k_not_multiple_of_passes(oracle_mod, den, torch_cuda, max_k):
     _, noisy = synth.noisy_image(200, 333, 0.5, synth.seed_for(23, max_k))
     for passes in (1, 4, 8):
         assert_same(oracle_mod, den, torch_cuda, noisy, 10, 1, max_k, passes=passes)
+
+
+@pytest.mark.parametrize("beta,passes", [(1, 1), (1, 4), (1, 8), (2, 2), (2, 4), (3, 1), (3, 2), (5, 1)])
+def test_fused_only_schedule(oracle_mod, den, torch_cuda, beta, passes):
+    """Repeated fused launches, whose first pass learns the previous launch's
+    changes from the per-pixel change bitmap."""
+    for i, (r, c) in enumerate(((200, 481), (131, 250), (64, 700))):
+        _, noisy = synth.noisy_image(r, c, 0.3, synth.seed_for(30, 10 * beta + i))
+        assert_same(oracle_mod, den, torch_cuda, noisy, 10, beta, 32 if beta < 3 else 12, passes=passes, kernel=2)
+
+
+@pytest.mark.parametrize("list_cap", [1, 7, 100, 1000])
+def test_list_overflow_falls_back_to_full_pass(oracle_mod, den, torch_cuda, list_cap):
+    """Change lists far smaller than the changes: list passes must switch to
+    evaluating every pixel and stay exact."""
+    for beta in (1, 2):
+        _, noisy = synth.noisy_image(150, 333, 0.4, synth.seed_for(31, beta))
+        for passes in (1, 2):
+            assert_same(oracle_mod, den, torch_cuda, noisy, 10, beta, 32, passes=passes, list_cap=list_cap)
 
 
 def test_unfused_kernel_every_beta(oracle_mod, den, torch_cuda):
