@@ -33,8 +33,7 @@ struct Ctrl {
     unsigned mask;       // bit t: pass t of the running launch changed a pixel
     unsigned work_launches;
     unsigned executed;   // passes executed by launches that did work
-    unsigned stamp;      // list-pass claim stamp (monotonic across calls, >= 1)
-    unsigned list_n[2];  // entries appended to change list 0 / 1 (> capacity: overflow)
+    unsigned list_n[3];  // entries appended to change list 0..2 (> capacity: overflow)
     // Pixel evaluations the passes needed (core pixels only: a dense pass
     // counts every image pixel, a list pass the pixels it claimed), by kernel.
     unsigned long long evals_fused;
@@ -55,12 +54,16 @@ struct PassArgs {
     // Null when unused.
     uint32_t* chg_maps;
     int map_words;            // words per image row
-    // Change lists (list passes): pixels changed by the last pass of launch
-    // L are appended, packed as (row << 16) | column, to list L & 1; its
-    // length is ctrl->list_n[L & 1].  Null when unused.
-    uint32_t* lists[2];
+    // Change lists and bitmaps (list passes): the pixels changed by the last
+    // pass of launch L are appended, packed as (row << 16) | column, to list
+    // L % 3 (length ctrl->list_n[L % 3]) and set in bitmap L % 3 (rows x
+    // bm_words 32-bit words, bit c & 31 of word c >> 5 of row r).  Launch L
+    // reads list / bitmap (L + 2) % 3 and clears bitmap (L + 1) % 3.  Null
+    // when unused.
+    uint32_t* lists[3];
     unsigned list_cap;
-    uint32_t* stamps;         // one claim stamp per image pixel (list passes)
+    uint32_t* bitmaps[3];
+    int bm_words;
     int write_prev;           // fused kernel: also write I_{t-1} to the third canvas
 };
 
@@ -96,11 +99,11 @@ __device__ __forceinline__ void finish_launch(Ctrl* c, unsigned cta_mask, int np
         c->cur = new_cur;
         c->aux = new_aux;
         const unsigned L = c->work_launches;
-        // The next launch appends to list (L + 1) & 1, which this launch read.
-        c->list_n[(L + 1u) & 1u] = 0u;
+        // The next launch appends to list (L + 1) % 3, which this launch used
+        // to clear its bitmap.
+        c->list_n[(L + 1u) % 3u] = 0u;
         c->work_launches = L + 1u;
         c->executed += (unsigned)np;
-        c->stamp += 1u;
         c->done = 0u;
         __threadfence();
     }

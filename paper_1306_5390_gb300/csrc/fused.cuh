@@ -558,8 +558,9 @@ fused_kernel(PassArgs a) {
     // next (list) pass starts from; an overflowed tile list forces that pass
     // to be dense.
     if (a.lists[0] != nullptr) {
-        uint32_t* glist = a.lists[L & 1u];
-        unsigned* gn = &a.ctrl->list_n[L & 1u];
+        uint32_t* glist = a.lists[L % 3u];
+        unsigned* gn = &a.ctrl->list_n[L % 3u];
+        uint32_t* gbm = a.bitmaps[L % 3u];
         if (nlast <= G::kListCap) {
             for (int base = warp * 32; base < nlast; base += G::kThreads) {
                 const int i = base + lane;
@@ -572,12 +573,13 @@ fused_kernel(PassArgs a) {
                     if (in_core_px(y, x, G::H, G::TH, G::TW) && gy < a.rows && gx < a.cols) {
                         want = true;
                         v = ((uint32_t)gy << 16) | (uint32_t)gx;
+                        atomicOr(gbm + (size_t)gy * a.bm_words + (gx >> 5), 1u << (gx & 31));
                     }
                 }
                 list_append(glist, gn, a.list_cap, want, v, lane);
             }
         } else if (tid == 0) {
-            atomicAdd(gn, a.list_cap + 1u);
+            atomicAdd(gn, a.list_cap + 1u);  // overflow: the next pass evaluates every pixel
         }
     }
     // The last pass's changed core pixels -> this launch's map (all core

@@ -93,9 +93,9 @@ __global__ void ctrl_init_kernel(Ctrl* c, unsigned max_k) {
     c->mask = 0;
     c->work_launches = 0;
     c->executed = 0;
-    if (c->stamp == 0) c->stamp = 1;  // stamps are never reset; 0 means "never claimed"
     c->list_n[0] = 0;
     c->list_n[1] = 0;
+    c->list_n[2] = 0;
     c->evals_fused = 0;
     c->evals_list = 0;
 }

@@ -32,10 +32,10 @@ struct hgrms_ctx {
     size_t canvas_bytes = 0;
     uint32_t* chg_maps = nullptr;  // three pixel change bitmaps (repeated fused launches)
     size_t chg_map_bytes = 0;
-    uint32_t* lists = nullptr;     // two change lists (list passes)
+    uint32_t* lists = nullptr;     // three change lists (list passes)
     size_t list_cap = 0;
-    uint32_t* stamps = nullptr;    // per-pixel claim stamps (list passes)
-    size_t stamp_count = 0;
+    uint32_t* bitmaps = nullptr;   // three per-pixel change bitmaps (list passes)
+    size_t bitmap_words = 0;
     hg::Ctrl* ctrl = nullptr;
     hg::Ctrl* host_ctrl = nullptr;
     int last_cuda_error = 0;
@@ -131,6 +131,7 @@ struct Plan {
     int fused_launches; // of which fused
     int map_words;
     size_t list_cap;
+    int bm_words;
 };
 
 int make_plan(hgrms_ctx* h, int rows, int cols, int beta, int max_k, Plan* p) {
@@ -138,6 +139,7 @@ int make_plan(hgrms_ctx* h, int rows, int cols, int beta, int max_k, Plan* p) {
     p->fused = p->schedule != kPlain;
     p->fe = nullptr;
     p->list_cap = 0;
+    p->bm_words = 0;
     if (p->fused) {
         p->T = h->opt_passes > 0 ? h->opt_passes : default_passes(beta);
         p->fe = find_fused(beta, p->T);
@@ -153,6 +155,7 @@ int make_plan(hgrms_ctx* h, int rows, int cols, int beta, int max_k, Plan* p) {
             p->map_words = 0;
             p->list_cap = h->opt_list_cap > 0 ? (size_t)h->opt_list_cap
                                               : (size_t)rows * (size_t)cols / 4 + 65536;
+            p->bm_words = (cols + 31) / 32 + 1;
         } else {
             p->fused_launches = p->launches = (max_k + p->T - 1) / p->T;
             p->map_words = (p->tiles_x * p->fe->TW + 31) / 32 + 2;
@@ -195,21 +198,20 @@ int ensure_maps(hgrms_ctx* h, size_t bytes) {
     return HGRMS_OK;
 }
 
-int ensure_lists(hgrms_ctx* h, size_t cap, size_t pixels) {
+int ensure_lists(hgrms_ctx* h, size_t cap, size_t bm_words) {
     if (cap > h->list_cap) {
         if (h->lists) cudaFree(h->lists);
         h->lists = nullptr;
         h->list_cap = 0;
-        HG_TRY(h, cudaMalloc(&h->lists, 2 * cap * sizeof(uint32_t)));
+        HG_TRY(h, cudaMalloc(&h->lists, 3 * cap * sizeof(uint32_t)));
         h->list_cap = cap;
     }
-    if (pixels > h->stamp_count) {
-        if (h->stamps) cudaFree(h->stamps);
-        h->stamps = nullptr;
-        h->stamp_count = 0;
-        HG_TRY(h, cudaMalloc(&h->stamps, pixels * sizeof(uint32_t)));
-        HG_TRY(h, cudaMemsetAsync(h->stamps, 0, pixels * sizeof(uint32_t), h->stream));
-        h->stamp_count = pixels;
+    if (bm_words > h->bitmap_words) {
+        if (h->bitmaps) cudaFree(h->bitmaps);
+        h->bitmaps = nullptr;
+        h->bitmap_words = 0;
+        HG_TRY(h, cudaMalloc(&h->bitmaps, 3 * bm_words * sizeof(uint32_t)));
+        h->bitmap_words = bm_words;
     }
     return HGRMS_OK;
 }
@@ -237,8 +239,9 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
         rc = ensure_maps(h, 3 * map_bytes);
         if (rc < 0) return rc;
     }
+    const size_t bm_size = (size_t)rows * (size_t)p.bm_words;
     if (p.list_cap > 0) {
-        rc = ensure_lists(h, p.list_cap, (size_t)rows * (size_t)cols);
+        rc = ensure_lists(h, p.list_cap, bm_size);
         if (rc < 0) return rc;
     }
     cudaStream_t s = h->stream;
@@ -252,6 +255,9 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     HG_TRY(h, hg::launch_ctrl_init(h->ctrl, (unsigned)max_k, s));
     // Map 0 is written by the first launch; the launches clear the others.
     if (p.map_words > 0) HG_TRY(h, cudaMemsetAsync(h->chg_maps, 0, map_bytes, s));
+    // The three change bitmaps start empty; each list pass clears the one the
+    // next pass writes.
+    if (p.list_cap > 0) HG_TRY(h, cudaMemsetAsync(h->bitmaps, 0, 3 * bm_size * sizeof(uint32_t), s));
     hg::PassArgs a;
     for (int i = 0; i < 3; ++i) a.canvas[i] = h->canvas[i];
     a.pitch = p.pitch;
@@ -262,10 +268,12 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     a.ctrl = h->ctrl;
     a.chg_maps = p.map_words > 0 ? h->chg_maps : nullptr;
     a.map_words = p.map_words;
-    a.lists[0] = p.list_cap > 0 ? h->lists : nullptr;
-    a.lists[1] = p.list_cap > 0 ? h->lists + p.list_cap : nullptr;
+    for (int i = 0; i < 3; ++i) {
+        a.lists[i] = p.list_cap > 0 ? h->lists + i * p.list_cap : nullptr;
+        a.bitmaps[i] = p.list_cap > 0 ? h->bitmaps + i * bm_size : nullptr;
+    }
     a.list_cap = (unsigned)p.list_cap;
-    a.stamps = h->stamps;
+    a.bm_words = p.bm_words;
     a.write_prev = p.schedule == kHybrid ? 1 : 0;
     // Per-launch timing is limited to calls of at most kMaxTimedLaunches launches.
     constexpr int kMaxTimedLaunches = 4096;
@@ -364,7 +372,7 @@ HG_EXPORT void hgrms_destroy(hgrms_t h) {
         if (h->ctrl) cudaFree(h->ctrl);
         if (h->chg_maps) cudaFree(h->chg_maps);
         if (h->lists) cudaFree(h->lists);
-        if (h->stamps) cudaFree(h->stamps);
+        if (h->bitmaps) cudaFree(h->bitmaps);
         if (h->host_ctrl) cudaFreeHost(h->host_ctrl);
         for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     }
