@@ -109,17 +109,59 @@ __device__ __forceinline__ void finish_launch(Ctrl* c, unsigned cta_mask, int np
     }
 }
 
-// Warp-aggregated append of this lane's value (when `want`) to a global list.
-// Every lane of the warp must call it.
-__device__ __forceinline__ void list_append(uint32_t* list, unsigned* n, unsigned cap, bool want, uint32_t v,
-                                            int lane) {
+// Appends to a global change list staged per warp in shared memory, so that
+// a CTA reserves space in the global list with one atomic (same-address
+// atomics from every warp of a large grid serialise in L2).
+struct StagedList {
+    static constexpr int kCap = 256;  // entries per warp buffer
+    uint32_t* buf;                    // this warp's buffer
+    int n;                            // entries in it (warp-uniform)
+};
+
+// Warp-collective: append this lane's value when `want`.  A buffer that
+// cannot take another full warp is written out with a warp-level atomic
+// (rare; only for CTAs with very many changes).
+__device__ __forceinline__ void staged_append(StagedList& sl, uint32_t* list, unsigned* n, unsigned cap, bool want,
+                                              uint32_t v, int lane) {
     const unsigned bal = __ballot_sync(0xffffffffu, want);
     if (!bal) return;
-    const int leader = __ffs(bal) - 1;
-    unsigned pos = 0;
-    if (lane == leader) pos = atomicAdd(n, (unsigned)__popc(bal));
-    pos = __shfl_sync(0xffffffffu, pos, leader) + (unsigned)__popc(bal & ((1u << lane) - 1u));
-    if (want && pos < cap) list[pos] = v;
+    if (sl.n > StagedList::kCap - 32) {
+        __syncwarp();
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(n, (unsigned)sl.n);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (int i = lane; i < sl.n; i += 32)
+            if (base + i < cap) list[base + i] = sl.buf[i];
+        __syncwarp();
+        sl.n = 0;
+    }
+    if (want) sl.buf[sl.n + __popc(bal & ((1u << lane) - 1u))] = v;
+    sl.n += __popc(bal);
+}
+
+// Block-collective (all threads): write every warp's staged entries to the
+// global list with one atomic per CTA.  `counts` is shared scratch of one int
+// per warp plus one.
+__device__ __forceinline__ void staged_flush(StagedList& sl, uint32_t* list, unsigned* n, unsigned cap,
+                                             int* counts, int nwarps) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    __syncwarp();
+    if (lane == 0) counts[warp] = sl.n;
+    __syncthreads();
+    if (tid == 0) {
+        int total = 0;
+        for (int w = 0; w < nwarps; ++w) {
+            const int c = counts[w];
+            counts[w] = total;
+            total += c;
+        }
+        counts[nwarps] = total ? (int)atomicAdd(n, (unsigned)total) : 0;
+    }
+    __syncthreads();
+    const unsigned base = (unsigned)counts[nwarps] + (unsigned)counts[warp];
+    for (int i = lane; i < sl.n; i += 32)
+        if (base + i < cap) list[base + i] = sl.buf[i];
+    sl.n = 0;
 }
 
 }  // namespace hg

@@ -78,7 +78,7 @@ struct FusedGeo {
     static constexpr size_t kListOff = kCandOff + (size_t)kWarps * kCandCap * sizeof(uint16_t);
     static constexpr size_t kMarkOff = kListOff + 2ull * kListCap * sizeof(uint16_t);
     static constexpr size_t kCntOff = kMarkOff + 2ull * kMarkWords * sizeof(uint32_t);
-    static constexpr size_t kSmem = kCntOff + 4 * sizeof(int);
+    static constexpr size_t kSmem = kCntOff + 8 * sizeof(int);
     // Lanes 0..31 cover columns [C0, C0 + 256): results within T*beta of
     // those edges may use wrong horizontal neighbours, so T*beta <= 8 keeps
     // the core [kPadX, kPadX + TW) exact after T passes.
@@ -555,29 +555,34 @@ fused_kernel(PassArgs a) {
     const int nlast = s_cnt[(np - 1) % 3];
     const uint16_t* last = lists + ((np - 1) & 1) * G::kListCap;
     // The last pass's changed core pixels -> the global change list that the
-    // next (list) pass starts from; an overflowed tile list forces that pass
-    // to be dense.
+    // next (list) pass starts from (one global atomic per CTA); an overflowed
+    // tile list forces that pass to evaluate every pixel.
     if (a.lists[0] != nullptr) {
         uint32_t* glist = a.lists[L % 3u];
         unsigned* gn = &a.ctrl->list_n[L % 3u];
         uint32_t* gbm = a.bitmaps[L % 3u];
+        int* s_sel = s_cnt + 4;  // [0]: core entries, [1]: global base
+        if (tid == 0) s_sel[0] = 0;
+        __syncthreads();
         if (nlast <= G::kListCap) {
-            for (int base = warp * 32; base < nlast; base += G::kThreads) {
-                const int i = base + lane;
-                bool want = false;
-                uint32_t v = 0;
-                if (i < nlast) {
-                    const int q = last[i];
-                    const int y = q / G::SW, x = q - y * G::SW;
-                    const int gy = y0 + y - G::H, gx = x0 + x - kPadX;
-                    if (in_core_px(y, x, G::H, G::TH, G::TW) && gy < a.rows && gx < a.cols) {
-                        want = true;
-                        v = ((uint32_t)gy << 16) | (uint32_t)gx;
-                        atomicOr(gbm + (size_t)gy * a.bm_words + (gx >> 5), 1u << (gx & 31));
-                    }
+            // Compact the core entries to the front of `cand` (free now).
+            uint32_t* sel = reinterpret_cast<uint32_t*>(smem + G::kCandOff);
+            for (int i = tid; i < nlast; i += G::kThreads) {
+                const int q = last[i];
+                const int y = q / G::SW, x = q - y * G::SW;
+                const int gy = y0 + y - G::H, gx = x0 + x - kPadX;
+                if (in_core_px(y, x, G::H, G::TH, G::TW) && gy < a.rows && gx < a.cols) {
+                    sel[atomicAdd(&s_sel[0], 1)] = ((uint32_t)gy << 16) | (uint32_t)gx;
+                    atomicOr(gbm + (size_t)gy * a.bm_words + (gx >> 5), 1u << (gx & 31));
                 }
-                list_append(glist, gn, a.list_cap, want, v, lane);
             }
+            __syncthreads();
+            const int nsel = s_sel[0];
+            if (tid == 0) s_sel[1] = nsel ? (int)atomicAdd(gn, (unsigned)nsel) : 0;
+            __syncthreads();
+            const unsigned gbase = (unsigned)s_sel[1];
+            for (int i = tid; i < nsel; i += G::kThreads)
+                if (gbase + i < a.list_cap) glist[gbase + i] = sel[i];
         } else if (tid == 0) {
             atomicAdd(gn, a.list_cap + 1u);  // overflow: the next pass evaluates every pixel
         }
@@ -607,14 +612,21 @@ fused_kernel(PassArgs a) {
             }
         }
     }
-    // Work accounting: dense passes evaluate every core pixel on the image.
+    // Work accounting (one global atomic per CTA): dense passes evaluate
+    // every core pixel on the image.
     {
-        unsigned long long ev = __reduce_add_sync(0xffffffffu, c.evals);
+        int* s_ev = s_cnt + 6;
+        if (tid == 0) s_ev[0] = 0;
+        __syncthreads();
+        const unsigned ev = __reduce_add_sync(0xffffffffu, c.evals);
+        if (lane == 0 && ev) atomicAdd(&s_ev[0], (int)ev);
+        __syncthreads();
         if (tid == 0) {
             const int ch = min(G::TH, a.rows - y0), cw = min(G::TW, a.cols - x0);
-            ev += (unsigned long long)dense_passes * (unsigned long long)(ch * cw);
+            const unsigned long long total =
+                (unsigned long long)s_ev[0] + (unsigned long long)dense_passes * (unsigned long long)(ch * cw);
+            if (total) atomicAdd(&a.ctrl->evals_fused, total);
         }
-        if (lane == 0 && ev) atomicAdd(&a.ctrl->evals_fused, ev);
     }
     if (tid == 0) finish_launch(a.ctrl, cta_mask, np, gridDim.x, aux, a.write_prev ? third : cur);
 }

@@ -62,8 +62,12 @@ __global__ void __launch_bounds__(256) list_kernel(PassArgs a) {
     __shared__ unsigned s_cur, s_aux, s_L, s_n, s_nclr;
     __shared__ uint8_t blk_all[kWarps][E * E];
     __shared__ uint32_t bmr_all[kWarps][E];
+    __shared__ uint32_t stage_all[kWarps][StagedList::kCap];
+    __shared__ int s_counts[kWarps + 1];
+    __shared__ unsigned long long s_evals;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
+        s_evals = 0ull;
         s_np = launch_passes(a.ctrl, 1);
         s_cur = __ldcg(&a.ctrl->cur);
         s_aux = __ldcg(&a.ctrl->aux);
@@ -105,6 +109,7 @@ __global__ void __launch_bounds__(256) list_kernel(PassArgs a) {
 
     bool any = false;
     unsigned evals = 0;
+    StagedList sl{stage_all[warp], 0};
     if (n <= a.list_cap) {
         uint8_t* blk = blk_all[warp];
         uint32_t* bmr = bmr_all[warp];
@@ -159,7 +164,7 @@ __global__ void __launch_bounds__(256) list_kernel(PassArgs a) {
                     }
                 }
                 any |= ch;
-                list_append(next, nnext, a.list_cap, ch, v, lane);
+                staged_append(sl, next, nnext, a.list_cap, ch, v, lane);
             }
             __syncwarp();
         }
@@ -186,13 +191,17 @@ __global__ void __launch_bounds__(256) list_kernel(PassArgs a) {
                 }
             }
             any |= ch;
-            list_append(next, nnext, a.list_cap, ch, v, lane);
+            staged_append(sl, next, nnext, a.list_cap, ch, v, lane);
         }
     }
-    const unsigned long long ev = __reduce_add_sync(0xffffffffu, evals);
-    if (lane == 0 && ev) atomicAdd(&a.ctrl->evals_list, ev);
+    staged_flush(sl, next, nnext, a.list_cap, s_counts, kWarps);
+    const unsigned ev = __reduce_add_sync(0xffffffffu, evals);
+    if (lane == 0 && ev) atomicAdd(&s_evals, (unsigned long long)ev);
     const int cta_any = __syncthreads_or(any);
-    if (tid == 0) finish_launch(a.ctrl, cta_any ? 1u : 0u, 1, gridDim.x, s_aux, s_cur);
+    if (tid == 0) {
+        if (s_evals) atomicAdd(&a.ctrl->evals_list, s_evals);
+        finish_launch(a.ctrl, cta_any ? 1u : 0u, 1, gridDim.x, s_aux, s_cur);
+    }
 }
 
 cudaError_t launch_list(int beta, const PassArgs& a, int sms, cudaStream_t s) {
