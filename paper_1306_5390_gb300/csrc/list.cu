@@ -4,11 +4,10 @@
 // A pixel's output in pass t depends only on its (2 beta + 1)^2 window in the
 // image of pass t-1, so a pixel with no changed pixel (in pass t-1) within
 // beta keeps its value.  The kernel walks the list of pixels the previous
-// pass changed; one warp takes one changed pixel p, stages the (4 beta + 1)^2
-// block of the current image around p and the matching block of the
-// previous pass's change bitmap in shared memory, and evaluates every pixel
-// q of p's window that p "owns": p is the first changed pixel, in raster
-// order, of q's window, so each pixel is evaluated exactly once.  Results go
+// pass changed; one thread takes one (changed pixel p, window offset) pair
+// and evaluates q = p + offset if p "owns" q: p is the first changed pixel,
+// in raster order, of q's window (read from the previous pass's change
+// bitmap), so each pixel is evaluated exactly once.  Results go
 // to the partner canvas, which already agrees with the current image at
 // every pixel that is not evaluated (see Ctrl); pixels that change form the
 // next list and bitmap.  When the previous list overflowed its capacity, the
@@ -31,7 +30,11 @@ __device__ __forceinline__ uint32_t row_bits(const uint32_t* __restrict__ row, i
 
 // Algorithm 2 for an interior pixel (card <= 2 is implied by flag >
 // pix_count - 3 for alpha >= 1, and card is 0 for alpha = 0).  `p` points at
-// the pixel in a row-major block with row stride `stride`.
+// the pixel in a row-major byte array with row stride `stride`.  sum < 2^24
+// and flag <= 225, so the float quotient is exact to well under the gap to
+// the next integer and its floor is floor(sum / flag); the square root is
+// correctly rounded, so its floor is the integer square root (sum / flag is
+// at most 255^2).
 template <int B>
 __device__ __forceinline__ int eval_pixel(const uint8_t* __restrict__ p, long long stride, int alpha) {
     const int ip = p[0];
@@ -41,27 +44,28 @@ __device__ __forceinline__ int eval_pixel(const uint8_t* __restrict__ p, long lo
 #pragma unroll
         for (int dx = -B; dx <= B; ++dx) {
             const int v = p[dy * stride + dx];
-            if (!(v < ip + alpha + 1 && v > ip - alpha)) {
-                sum += v * v;
-                ++flag;
-            }
+            const bool open = !(v < ip + alpha + 1 && v > ip - alpha);
+            sum += open ? v * v : 0;
+            flag += open ? 1 : 0;
         }
     constexpr int kPixCount = (2 * B + 1) * (2 * B + 1);
-    if (flag > kPixCount - 3) return (int)floorf(__fsqrt_rn((float)(sum / flag)));
+    if (flag > kPixCount - 3) {
+        const float q = floorf(__fdiv_rn((float)sum, (float)flag));
+        return (int)floorf(__fsqrt_rn(q));
+    }
     return ip;
 }
 
 }  // namespace
 
+constexpr int kListThreads = 512;
+
 template <int B>
-__global__ void __launch_bounds__(256) list_kernel(PassArgs a) {
+__global__ void __launch_bounds__(kListThreads, 2) list_kernel(PassArgs a) {
     constexpr int W = 2 * B + 1, P = W * W;
-    constexpr int E = 4 * B + 1;  // staged block side
-    constexpr int kWarps = 8;
+    constexpr int kWarps = kListThreads / 32;
     __shared__ int s_np;
     __shared__ unsigned s_cur, s_aux, s_L, s_n, s_nclr;
-    __shared__ uint8_t blk_all[kWarps][E * E];
-    __shared__ uint32_t bmr_all[kWarps][E];
     __shared__ uint32_t stage_all[kWarps][StagedList::kCap];
     __shared__ int s_counts[kWarps + 1];
     __shared__ unsigned long long s_evals;
@@ -88,6 +92,7 @@ __global__ void __launch_bounds__(256) list_kernel(PassArgs a) {
     const unsigned n = s_n;
     const long long gthreads = (long long)gridDim.x * blockDim.x;
     const long long gtid = (long long)blockIdx.x * blockDim.x + tid;
+    const long long warp_base = (long long)blockIdx.x * blockDim.x + (tid & ~31);
 
     // Clear the bitmap of pass L - 2 (written two launches ago, read by the
     // previous launch) for the next launch: walk its list, or clear it all if
@@ -111,67 +116,51 @@ __global__ void __launch_bounds__(256) list_kernel(PassArgs a) {
     unsigned evals = 0;
     StagedList sl{stage_all[warp], 0};
     if (n <= a.list_cap) {
-        uint8_t* blk = blk_all[warp];
-        uint32_t* bmr = bmr_all[warp];
-        const long long nwarps = gthreads / 32;
-        for (long long e = gtid / 32; e < n; e += nwarps) {
-            const uint32_t pk = prev[e];
-            const int py = (int)(pk >> 16), px = (int)(pk & 0xffffu);
-            // Stage the image block [py - 2B, py + 2B] x [px - 2B, px + 2B]
-            // (rows/columns off the image read canvas padding; only interior
-            // pixels are evaluated, and their windows lie on the image).
-            for (int j = lane; j < E * E; j += 32) {
-                const int by = j / E, bx = j - by * E;
-                blk[j] = in[(long long)(py + by - 2 * B) * a.pitch + (px + bx - 2 * B)];
-            }
-            if (lane < E) {
-                const int gy = py + lane - 2 * B;
-                bmr[lane] = (gy >= 0 && gy < a.rows)
-                                ? row_bits(bm_prev + (size_t)gy * a.bm_words, a.bm_words, px - 2 * B)
-                                : 0u;
-            }
-            __syncwarp();
-            for (int base = 0; base < P; base += 32) {
-                const int j = base + lane;
-                bool ch = false;
-                uint32_t v = 0;
-                if (j < P) {
-                    const int dy = j / W - B, dx = j - (j / W) * W - B;
-                    const int y = py + dy, x = px + dx;
-                    const int cy = 2 * B + dy, cx = 2 * B + dx;  // block coordinates of q
-                    if (y >= B && y < a.rows - B && x >= B && x < a.cols - B) {
-                        // p owns q unless a changed pixel before p (raster
-                        // order) lies in q's window.
-                        const uint32_t wm = ((1u << W) - 1u) << (cx - B);
-                        bool owner = true;
-#pragma unroll
-                        for (int r = 0; r < W; ++r) {
-                            const int by = cy - B + r;
-                            if (by < 2 * B && (bmr[by] & wm)) owner = false;
-                            if (by == 2 * B && (bmr[by] & wm & ((1u << (2 * B)) - 1u))) owner = false;
-                        }
-                        if (owner) {
-                            ++evals;
-                            const int ip = blk[cy * E + cx];
-                            const int nv = eval_pixel<B>(blk + cy * E + cx, E, a.alpha);
-                            out[(long long)y * a.pitch + x] = (uint8_t)nv;
-                            if (nv != ip) {
-                                ch = true;
-                                v = ((uint32_t)y << 16) | (uint32_t)x;
-                                atomicOr(bm_next + (size_t)y * a.bm_words + (x >> 5), 1u << (x & 31));
-                            }
+        // One thread per (changed pixel p, window offset) pair: q = p + offset
+        // is evaluated by the thread of the first changed pixel of q's window
+        // in raster order ("owner"), found in the previous pass's bitmap.
+        const long long total = (long long)n * P;
+        for (long long base = warp_base; base < total; base += gthreads) {
+            const long long i = base + lane;
+            bool ch = false;
+            uint32_t v = 0;
+            if (i < total) {
+                const unsigned e = (unsigned)(i / P);
+                const int o = (int)(i - (long long)e * P);
+                const int dy = o / W - B, dx = o - (o / W) * W - B;
+                const uint32_t pk = __ldg(prev + e);
+                const int py = (int)(pk >> 16), px = (int)(pk & 0xffffu);
+                const int y = py + dy, x = px + dx;
+                if (y >= B && y < a.rows - B && x >= B && x < a.cols - B) {
+                    bool owner = true;
+                    // rows of q's window above p's row: any changed pixel there comes first
+                    for (int r = y - B; r < py && owner; ++r)
+                        if (row_bits(bm_prev + (size_t)r * a.bm_words, a.bm_words, x - B) & ((1u << W) - 1u))
+                            owner = false;
+                    // p's row: changed pixels left of p in q's window come first
+                    if (owner && B - dx > 0 &&
+                        (row_bits(bm_prev + (size_t)py * a.bm_words, a.bm_words, x - B) & ((1u << (B - dx)) - 1u)))
+                        owner = false;
+                    if (owner) {
+                        ++evals;
+                        const long long off = (long long)y * a.pitch + x;
+                        const int ip = in[off];
+                        const int nv = eval_pixel<B>(in + off, a.pitch, a.alpha);
+                        out[off] = (uint8_t)nv;
+                        if (nv != ip) {
+                            ch = true;
+                            v = ((uint32_t)y << 16) | (uint32_t)x;
+                            atomicOr(bm_next + (size_t)y * a.bm_words + (x >> 5), 1u << (x & 31));
                         }
                     }
                 }
-                any |= ch;
-                staged_append(sl, next, nnext, a.list_cap, ch, v, lane);
             }
-            __syncwarp();
+            any |= ch;
+            staged_append(sl, next, nnext, a.list_cap, ch, v, lane);
         }
     } else {
         // Previous list overflowed: evaluate and write every pixel.
         const long long total = (long long)a.rows * a.cols;
-        const long long warp_base = (long long)blockIdx.x * blockDim.x + (tid & ~31);
         for (long long base = warp_base; base < total; base += gthreads) {
             const long long i = base + lane;
             bool ch = false;
@@ -205,15 +194,15 @@ __global__ void __launch_bounds__(256) list_kernel(PassArgs a) {
 }
 
 cudaError_t launch_list(int beta, const PassArgs& a, int sms, cudaStream_t s) {
-    const unsigned grid = (unsigned)sms * 8u;
+    const unsigned grid = (unsigned)sms * 2u;
     switch (beta) {
-        case 1: list_kernel<1><<<grid, 256, 0, s>>>(a); break;
-        case 2: list_kernel<2><<<grid, 256, 0, s>>>(a); break;
-        case 3: list_kernel<3><<<grid, 256, 0, s>>>(a); break;
-        case 4: list_kernel<4><<<grid, 256, 0, s>>>(a); break;
-        case 5: list_kernel<5><<<grid, 256, 0, s>>>(a); break;
-        case 6: list_kernel<6><<<grid, 256, 0, s>>>(a); break;
-        case 7: list_kernel<7><<<grid, 256, 0, s>>>(a); break;
+        case 1: list_kernel<1><<<grid, kListThreads, 0, s>>>(a); break;
+        case 2: list_kernel<2><<<grid, kListThreads, 0, s>>>(a); break;
+        case 3: list_kernel<3><<<grid, kListThreads, 0, s>>>(a); break;
+        case 4: list_kernel<4><<<grid, kListThreads, 0, s>>>(a); break;
+        case 5: list_kernel<5><<<grid, kListThreads, 0, s>>>(a); break;
+        case 6: list_kernel<6><<<grid, kListThreads, 0, s>>>(a); break;
+        case 7: list_kernel<7><<<grid, kListThreads, 0, s>>>(a); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
