@@ -95,9 +95,9 @@ int hgrms_last_cuda_error(hgrms_t h);
 /* ---- Tuning and measurement (not part of the method) ------------------ */
 
 /* Options for hgrms_set_option. */
-#define HGRMS_OPT_KERNEL   1 /* 0 = one fused multi-pass tile launch, then one list-pass launch per
-                                 remaining pass (default); 1 = unfused one-pass kernel for every
-                                 pass; 2 = fused tile launches only */
+#define HGRMS_OPT_KERNEL   1 /* 0 = one fused multi-pass tile launch, then one persistent launch that
+                                 runs every remaining pass as a list pass (default); 1 = unfused
+                                 one-pass kernel for every pass; 2 = fused tile launches only */
 #define HGRMS_OPT_PASSES   2 /* passes fused per launch; 0 = the built-in choice for beta */
 #define HGRMS_OPT_TIMING   3 /* 1 = time every denoising launch with CUDA events (see hgrms_stats) */
 #define HGRMS_OPT_LIST_CAP 4 /* capacity of the change lists of list passes (0 = rows*cols/4 + 65536);
@@ -133,7 +133,7 @@ int hgrms_stats(hgrms_t h, hgrms_stats_t* out);
 
 /* Per-launch durations (ms) of the last call, recorded when HGRMS_OPT_TIMING
  * is on, in launch order; kind[i] (if kind is not NULL) is 0 for a fused tile
- * launch, 1 for a list pass, 2 for an unfused pass.  Copies at most n entries
+ * launch, 1 for the launch running the list passes, 2 for an unfused pass.  Copies at most n entries
  * and returns the number recorded, or HGRMS_EINVAL. */
 int hgrms_launch_times(hgrms_t h, float* ms, int* kind, int n);
 

@@ -33,7 +33,11 @@ struct Ctrl {
     unsigned mask;       // bit t: pass t of the running launch changed a pixel
     unsigned work_launches;
     unsigned executed;   // passes executed by launches that did work
-    unsigned list_n[3];  // entries appended to change list 0..2 (> capacity: overflow)
+    unsigned list_n[4];  // entries appended to change list 0..3 (> capacity: overflow)
+    unsigned changed[3]; // list-pass loop: pass t sets changed[t % 3]
+    unsigned bar_count;  // grid barrier of the list-pass loop: arrivals
+    unsigned bar_gen;    // grid barrier generation
+    unsigned error;      // 1: a bounded device wait gave up
     // Pixel evaluations the passes needed (core pixels only: a dense pass
     // counts every image pixel, a list pass the pixels it claimed), by kernel.
     unsigned long long evals_fused;
@@ -54,15 +58,15 @@ struct PassArgs {
     // Null when unused.
     uint32_t* chg_maps;
     int map_words;            // words per image row
-    // Change lists and bitmaps (list passes): the pixels changed by the last
-    // pass of launch L are appended, packed as (row << 16) | column, to list
-    // L % 3 (length ctrl->list_n[L % 3]) and set in bitmap L % 3 (rows x
-    // bm_words 32-bit words, bit c & 31 of word c >> 5 of row r).  Launch L
-    // reads list / bitmap (L + 2) % 3 and clears bitmap (L + 1) % 3.  Null
-    // when unused.
-    uint32_t* lists[3];
+    // Change lists and bitmaps (list passes): changed pixels are appended,
+    // packed as (row << 16) | column, to a list (length ctrl->list_n[i]) and
+    // set in the matching bitmap (rows x bm_words 32-bit words, bit c & 31 of
+    // word c >> 5 of row r).  The fused launch writes set 0 with its last
+    // pass; list pass t of the list-pass loop reads set t % 4, writes set
+    // (t + 1) % 4 and clears bitmap (t + 3) % 4.  Null when unused.
+    uint32_t* lists[4];
     unsigned list_cap;
-    uint32_t* bitmaps[3];
+    uint32_t* bitmaps[4];
     int bm_words;
     int write_prev;           // fused kernel: also write I_{t-1} to the third canvas
 };
@@ -98,11 +102,7 @@ __device__ __forceinline__ void finish_launch(Ctrl* c, unsigned cta_mask, int np
         if (ones < (unsigned)np) c->converged = 1u;
         c->cur = new_cur;
         c->aux = new_aux;
-        const unsigned L = c->work_launches;
-        // The next launch appends to list (L + 1) % 3, which this launch used
-        // to clear its bitmap.
-        c->list_n[(L + 1u) % 3u] = 0u;
-        c->work_launches = L + 1u;
+        c->work_launches += 1u;
         c->executed += (unsigned)np;
         c->done = 0u;
         __threadfence();

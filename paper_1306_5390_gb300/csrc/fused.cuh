@@ -558,9 +558,9 @@ fused_kernel(PassArgs a) {
     // next (list) pass starts from (one global atomic per CTA); an overflowed
     // tile list forces that pass to evaluate every pixel.
     if (a.lists[0] != nullptr) {
-        uint32_t* glist = a.lists[L % 3u];
-        unsigned* gn = &a.ctrl->list_n[L % 3u];
-        uint32_t* gbm = a.bitmaps[L % 3u];
+        uint32_t* glist = a.lists[0];
+        unsigned* gn = &a.ctrl->list_n[0];
+        uint32_t* gbm = a.bitmaps[0];
         int* s_sel = s_cnt + 4;  // [0]: core entries, [1]: global base
         if (tid == 0) s_sel[0] = 0;
         __syncthreads();

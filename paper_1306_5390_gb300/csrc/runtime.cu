@@ -32,9 +32,9 @@ struct hgrms_ctx {
     size_t canvas_bytes = 0;
     uint32_t* chg_maps = nullptr;  // three pixel change bitmaps (repeated fused launches)
     size_t chg_map_bytes = 0;
-    uint32_t* lists = nullptr;     // three change lists (list passes)
+    uint32_t* lists = nullptr;     // four change lists (list passes)
     size_t list_cap = 0;
-    uint32_t* bitmaps = nullptr;   // three per-pixel change bitmaps (list passes)
+    uint32_t* bitmaps = nullptr;   // four per-pixel change bitmaps (list passes)
     size_t bitmap_words = 0;
     hg::Ctrl* ctrl = nullptr;
     hg::Ctrl* host_ctrl = nullptr;
@@ -151,7 +151,7 @@ int make_plan(hgrms_ctx* h, int rows, int cols, int beta, int max_k, Plan* p) {
         p->crows = hg::kPadY + (long long)p->tiles_y * p->fe->TH + 16;
         if (p->schedule == kHybrid) {
             p->fused_launches = max_k > 0 ? 1 : 0;
-            p->launches = max_k > p->T ? 1 + (max_k - p->T) : p->fused_launches;
+            p->launches = max_k > p->T ? 2 : p->fused_launches;  // + one launch running every list pass
             p->map_words = 0;
             p->list_cap = h->opt_list_cap > 0 ? (size_t)h->opt_list_cap
                                               : (size_t)rows * (size_t)cols / 4 + 65536;
@@ -203,14 +203,14 @@ int ensure_lists(hgrms_ctx* h, size_t cap, size_t bm_words) {
         if (h->lists) cudaFree(h->lists);
         h->lists = nullptr;
         h->list_cap = 0;
-        HG_TRY(h, cudaMalloc(&h->lists, 3 * cap * sizeof(uint32_t)));
+        HG_TRY(h, cudaMalloc(&h->lists, 4 * cap * sizeof(uint32_t)));
         h->list_cap = cap;
     }
     if (bm_words > h->bitmap_words) {
         if (h->bitmaps) cudaFree(h->bitmaps);
         h->bitmaps = nullptr;
         h->bitmap_words = 0;
-        HG_TRY(h, cudaMalloc(&h->bitmaps, 3 * bm_words * sizeof(uint32_t)));
+        HG_TRY(h, cudaMalloc(&h->bitmaps, 4 * bm_words * sizeof(uint32_t)));
         h->bitmap_words = bm_words;
     }
     return HGRMS_OK;
@@ -255,9 +255,8 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     HG_TRY(h, hg::launch_ctrl_init(h->ctrl, (unsigned)max_k, s));
     // Map 0 is written by the first launch; the launches clear the others.
     if (p.map_words > 0) HG_TRY(h, cudaMemsetAsync(h->chg_maps, 0, map_bytes, s));
-    // The three change bitmaps start empty; each list pass clears the one the
-    // next pass writes.
-    if (p.list_cap > 0) HG_TRY(h, cudaMemsetAsync(h->bitmaps, 0, 3 * bm_size * sizeof(uint32_t), s));
+    // The change bitmaps start empty; each list pass clears one for a later pass.
+    if (p.list_cap > 0) HG_TRY(h, cudaMemsetAsync(h->bitmaps, 0, 4 * bm_size * sizeof(uint32_t), s));
     hg::PassArgs a;
     for (int i = 0; i < 3; ++i) a.canvas[i] = h->canvas[i];
     a.pitch = p.pitch;
@@ -268,7 +267,7 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     a.ctrl = h->ctrl;
     a.chg_maps = p.map_words > 0 ? h->chg_maps : nullptr;
     a.map_words = p.map_words;
-    for (int i = 0; i < 3; ++i) {
+    for (int i = 0; i < 4; ++i) {
         a.lists[i] = p.list_cap > 0 ? h->lists + i * p.list_cap : nullptr;
         a.bitmaps[i] = p.list_cap > 0 ? h->bitmaps + i * bm_size : nullptr;
     }
@@ -322,6 +321,10 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
             else
                 h->stats.idle_kernel_ms += ms;
         }
+    }
+    if (c.error) {
+        h->last_cuda_error = 0;
+        return HGRMS_ETIMEOUT;
     }
     h->stats.passes_executed += (int)c.executed;
     h->stats.evals_fused += (long long)c.evals_fused;
