@@ -18,7 +18,7 @@
 // current canvas itself from values that are final at the barrier, so one
 // barrier per pass suffices; four list/bitmap sets rotate so that each set
 // is reset or cleared only while no CTA can still touch it.  Waits at the
-// barrier are bounded: after about a second the kernel records an error and
+// barrier are bounded: after one to two seconds the kernel records an error and
 // returns, and the call reports HGRMS_ETIMEOUT.
 #include "common.cuh"
 #include "kernels.h"
