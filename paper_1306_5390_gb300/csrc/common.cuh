@@ -35,13 +35,27 @@ struct Ctrl {
     unsigned executed;   // passes executed by launches that did work
     unsigned list_n[4];  // entries appended to change list 0..3 (> capacity: overflow)
     unsigned changed[3]; // list-pass loop: pass t sets changed[t % 3]
-    unsigned bar_count;  // grid barrier of the list-pass loop: arrivals
-    unsigned bar_gen;    // grid barrier generation
     unsigned error;      // 1: a bounded device wait gave up
     // Pixel evaluations the passes needed (core pixels only: a dense pass
     // counts every image pixel, a list pass the pixels it claimed), by kernel.
     unsigned long long evals_fused;
     unsigned long long evals_list;
+};
+
+// Grid barrier of the list-pass loop: CTAs arrive in groups, the last CTA of
+// every group arrives at the root, and the last root arrival releases every
+// group; each counter and each group's release word has its own 128-byte
+// line, so arrivals and polling do not queue behind one hot line.  All zero
+// at the start of a call.
+constexpr int kBarGroups = 16;
+struct alignas(128) BarLine {
+    unsigned v;
+    unsigned pad[31];
+};
+struct GridBar {
+    BarLine root;
+    BarLine count[kBarGroups];
+    BarLine gen[kBarGroups];
 };
 
 struct PassArgs {
@@ -69,6 +83,7 @@ struct PassArgs {
     uint32_t* bitmaps[4];
     int bm_words;
     int write_prev;           // fused kernel: also write I_{t-1} to the third canvas
+    GridBar* bar;             // list-pass loop barrier
 };
 
 // Passes the launch must run: 0 when the call has finished.

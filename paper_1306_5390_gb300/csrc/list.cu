@@ -66,31 +66,37 @@ __device__ __forceinline__ int eval_pixel(const uint8_t* p, long long stride, in
     return ip;
 }
 
-// Grid-wide barrier over co-resident CTAs, with a bounded wait.  Returns
-// false (for every thread of the CTA) when the wait gave up.
-__device__ __forceinline__ bool grid_barrier(Ctrl* c, unsigned nblocks, unsigned& gen) {
+// Grid-wide barrier over co-resident CTAs (see GridBar), with a bounded
+// wait.  Returns false (for every thread of the CTA) when the wait gave up.
+__device__ __forceinline__ bool grid_barrier(GridBar* b, Ctrl* c, unsigned nblocks, unsigned& gen) {
     __syncthreads();
     int ok = 1;
     if (threadIdx.x == 0) {
         const unsigned g = gen;
+        const unsigned ng = nblocks < (unsigned)kBarGroups ? nblocks : (unsigned)kBarGroups;
+        const unsigned grp = blockIdx.x % ng;
+        const unsigned gsize = (nblocks - grp + ng - 1u) / ng;
         __threadfence();
-        if (atomicAdd(&c->bar_count, 1u) == nblocks - 1u) {
-            c->bar_count = 0u;
+        if (atomicAdd(&b->count[grp].v, 1u) == gsize - 1u) {
+            b->count[grp].v = 0u;
             __threadfence();
-            atomicExch(&c->bar_gen, g + 1u);
-        } else {
-            unsigned spins = 0;
-            while (true) {
-                unsigned cur;
-                asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&c->bar_gen) : "memory");
-                if (cur != g) break;
-                if (++spins > (1u << 21)) {  // one to two seconds with the sleeps below
-                    atomicExch(&c->error, 1u);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(64);
+            if (atomicAdd(&b->root.v, 1u) == ng - 1u) {
+                b->root.v = 0u;
+                __threadfence();
+                for (unsigned j = 0; j < ng; ++j) atomicExch(&b->gen[j].v, g + 1u);
             }
+        }
+        unsigned spins = 0;
+        while (true) {
+            unsigned cur;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&b->gen[grp].v) : "memory");
+            if (cur != g) break;
+            if (++spins > (1u << 22)) {  // one to two seconds
+                atomicExch(&c->error, 1u);
+                ok = 0;
+                break;
+            }
+            if (spins > 64) __nanosleep(32);
         }
         __threadfence();
         gen = g + 1u;
@@ -119,7 +125,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
         s_cur = __ldcg(&ctrl->cur);
         s_aux = __ldcg(&ctrl->aux);
         s_maxk = __ldcg(&ctrl->max_k);
-        s_gen = __ldcg(&ctrl->bar_gen);
+        s_gen = 0u;  // the barrier struct is zeroed at the start of every call
     }
     __syncthreads();
     if (s_np == 0) return;  // the fused launch already finished the call
@@ -174,28 +180,36 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
             // One thread per (changed pixel p, window offset) pair; q = p +
             // offset is evaluated by the thread of its owner.
             const long long total = (long long)n * P;
-            for (long long base = warp_base; base < total; base += gthreads) {
-                const long long i = base + lane;
+            // The list entry of the next iteration is loaded one iteration early.
+            long long i = warp_base + lane;
+            uint32_t pk = i < total ? __ldcg(prev + (unsigned)(i / P)) : 0u;
+            for (long long base = warp_base; base < total; base += gthreads, i += gthreads) {
+                const long long inext = i + gthreads;
+                const uint32_t pk_next = inext < total ? __ldcg(prev + (unsigned)(inext / P)) : 0u;
                 bool ch = false;
                 uint32_t v = 0;
                 if (i < total) {
-                    const unsigned e = (unsigned)(i / P);
-                    const int o = (int)(i - (long long)e * P);
+                    const int o = (int)(i % P);
                     const int dy = o / W - B, dx = o - (o / W) * W - B;
-                    const uint32_t pk = __ldcg(prev + e);
                     const int py = (int)(pk >> 16), px = (int)(pk & 0xffffu);
                     const int y = py + dy, x = px + dx;
                     if (y >= B && y < a.rows - B && x >= B && x < a.cols - B) {
+                        // Ownership: no changed pixel of q's window precedes p
+                        // in raster order (rows above p's, then p's row left
+                        // of p).  All bitmap rows are loaded before testing.
+                        uint32_t rb[2 * B + 1];
+#pragma unroll
+                        for (int r = 0; r <= 2 * B; ++r) {
+                            const int gy = y - B + r;
+                            rb[r] = (gy <= py) ? row_bits(bm_prev + (size_t)gy * a.bm_words, a.bm_words, x - B) : 0u;
+                        }
                         bool owner = true;
-                        // rows of q's window above p's row: any changed pixel there comes first
-                        for (int r = y - B; r < py && owner; ++r)
-                            if (row_bits(bm_prev + (size_t)r * a.bm_words, a.bm_words, x - B) & ((1u << W) - 1u))
-                                owner = false;
-                        // p's row: changed pixels left of p in q's window come first
-                        if (owner && B - dx > 0 &&
-                            (row_bits(bm_prev + (size_t)py * a.bm_words, a.bm_words, x - B) &
-                             ((1u << (B - dx)) - 1u)))
-                            owner = false;
+#pragma unroll
+                        for (int r = 0; r <= 2 * B; ++r) {
+                            const int gy = y - B + r;
+                            if (gy < py && (rb[r] & ((1u << W) - 1u))) owner = false;
+                            if (gy == py && B - dx > 0 && (rb[r] & ((1u << (B - dx)) - 1u))) owner = false;
+                        }
                         if (owner) {
                             ++evals;
                             const long long off = (long long)y * a.pitch + x;
@@ -212,6 +226,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
                 }
                 any |= ch;
                 staged_append(sl, next, nnext, a.list_cap, ch, v, lane);
+                pk = pk_next;
             }
         } else {
             // Previous list overflowed: evaluate and write every pixel.
@@ -242,7 +257,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
         staged_flush(sl, next, nnext, a.list_cap, s_counts, kWarps);
         if (__syncthreads_or(any) && tid == 0) ctrl->changed[t % 3] = 1u;
         ++passes;
-        if (!grid_barrier(ctrl, gridDim.x, gen)) {
+        if (!grid_barrier(a.bar, ctrl, gridDim.x, gen)) {
             failed = true;
             break;
         }

@@ -36,6 +36,7 @@ struct hgrms_ctx {
     size_t list_cap = 0;
     uint32_t* bitmaps = nullptr;   // four per-pixel change bitmaps (list passes)
     size_t bitmap_words = 0;
+    hg::GridBar* bar = nullptr;    // list-pass loop barrier
     hg::Ctrl* ctrl = nullptr;
     hg::Ctrl* host_ctrl = nullptr;
     int last_cuda_error = 0;
@@ -256,7 +257,10 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     // Map 0 is written by the first launch; the launches clear the others.
     if (p.map_words > 0) HG_TRY(h, cudaMemsetAsync(h->chg_maps, 0, map_bytes, s));
     // The change bitmaps start empty; each list pass clears one for a later pass.
-    if (p.list_cap > 0) HG_TRY(h, cudaMemsetAsync(h->bitmaps, 0, 4 * bm_size * sizeof(uint32_t), s));
+    if (p.list_cap > 0) {
+        HG_TRY(h, cudaMemsetAsync(h->bitmaps, 0, 4 * bm_size * sizeof(uint32_t), s));
+        HG_TRY(h, cudaMemsetAsync(h->bar, 0, sizeof(hg::GridBar), s));
+    }
     hg::PassArgs a;
     for (int i = 0; i < 3; ++i) a.canvas[i] = h->canvas[i];
     a.pitch = p.pitch;
@@ -273,6 +277,7 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     }
     a.list_cap = (unsigned)p.list_cap;
     a.bm_words = p.bm_words;
+    a.bar = h->bar;
     a.write_prev = p.schedule == kHybrid ? 1 : 0;
     // Per-launch timing is limited to calls of at most kMaxTimedLaunches launches.
     constexpr int kMaxTimedLaunches = 4096;
@@ -354,6 +359,7 @@ HG_EXPORT int hgrms_create(hgrms_t* out, int device, void* cuda_stream) {
     int rc = HGRMS_OK;
     cudaError_t e = cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaMalloc(&h->ctrl, sizeof(hg::Ctrl));
+    if (e == cudaSuccess) e = cudaMalloc(&h->bar, sizeof(hg::GridBar));
     if (e == cudaSuccess) e = cudaMemset(h->ctrl, 0, sizeof(hg::Ctrl));
     if (e == cudaSuccess) e = cudaMallocHost(&h->host_ctrl, sizeof(hg::Ctrl));
     if (e != cudaSuccess) {
@@ -373,6 +379,7 @@ HG_EXPORT void hgrms_destroy(hgrms_t h) {
         for (int i = 0; i < 3; ++i)
             if (h->canvas[i]) cudaFree(h->canvas[i]);
         if (h->ctrl) cudaFree(h->ctrl);
+        if (h->bar) cudaFree(h->bar);
         if (h->chg_maps) cudaFree(h->chg_maps);
         if (h->lists) cudaFree(h->lists);
         if (h->bitmaps) cudaFree(h->bitmaps);
