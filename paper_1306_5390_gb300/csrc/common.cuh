@@ -34,7 +34,6 @@ struct Ctrl {
     unsigned work_launches;
     unsigned executed;   // passes executed by launches that did work
     unsigned list_n[4];  // entries appended to change list 0..3 (> capacity: overflow)
-    unsigned changed[3]; // list-pass loop: pass t sets changed[t % 3]
     unsigned error;      // 1: a bounded device wait gave up
     // Pixel evaluations the passes needed (core pixels only: a dense pass
     // counts every image pixel, a list pass the pixels it claimed), by kernel.

@@ -66,31 +66,43 @@ __device__ __forceinline__ int eval_pixel(const uint8_t* p, long long stride, in
     return ip;
 }
 
-// Grid-wide barrier over co-resident CTAs (see GridBar), with a bounded
-// wait.  Returns false (for every thread of the CTA) when the wait gave up.
-__device__ __forceinline__ bool grid_barrier(GridBar* b, Ctrl* c, unsigned nblocks, unsigned& gen) {
-    __syncthreads();
+__device__ __forceinline__ void store_release(unsigned* p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// Grid-wide barrier over co-resident CTAs (see GridBar) that also ORs one
+// flag over all CTAs.  Arrival counts sit in the low 16 bits of the group and
+// root counters and flag counts in the high bits; the release word of
+// barrier number b is 2b + (OR of the flags).  Every CTA gets the OR through
+// *flag.  The wait is bounded; returns false (for every thread of the CTA)
+// when it gave up.
+__device__ __forceinline__ bool grid_barrier(GridBar* b, Ctrl* c, unsigned nblocks, unsigned& nbar, int* flag) {
+    __shared__ int s_flag;
+    const int mine = __syncthreads_or(*flag);
     int ok = 1;
     if (threadIdx.x == 0) {
-        const unsigned g = gen;
+        const unsigned bn = nbar + 1u;
         const unsigned ng = nblocks < (unsigned)kBarGroups ? nblocks : (unsigned)kBarGroups;
         const unsigned grp = blockIdx.x % ng;
         const unsigned gsize = (nblocks - grp + ng - 1u) / ng;
         __threadfence();
-        if (atomicAdd(&b->count[grp].v, 1u) == gsize - 1u) {
+        const unsigned og = atomicAdd(&b->count[grp].v, 1u + (mine ? 0x10000u : 0u));
+        if ((og & 0xffffu) == gsize - 1u) {
+            const unsigned gflag = ((og >> 16) + (mine ? 1u : 0u)) ? 1u : 0u;
             b->count[grp].v = 0u;
             __threadfence();
-            if (atomicAdd(&b->root.v, 1u) == ng - 1u) {
+            const unsigned orr = atomicAdd(&b->root.v, 1u + (gflag << 16));
+            if ((orr & 0xffffu) == ng - 1u) {
+                const unsigned all = ((orr >> 16) + gflag) ? 1u : 0u;
                 b->root.v = 0u;
                 __threadfence();
-                for (unsigned j = 0; j < ng; ++j) atomicExch(&b->gen[j].v, g + 1u);
+                for (unsigned j = 0; j < ng; ++j) store_release(&b->gen[j].v, 2u * bn + all);
             }
         }
-        unsigned spins = 0;
+        unsigned spins = 0, word = 0;
         while (true) {
-            unsigned cur;
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(cur) : "l"(&b->gen[grp].v) : "memory");
-            if (cur != g) break;
+            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(word) : "l"(&b->gen[grp].v) : "memory");
+            if ((word >> 1) == bn) break;
             if (++spins > (1u << 22)) {  // one to two seconds
                 atomicExch(&c->error, 1u);
                 ok = 0;
@@ -98,10 +110,28 @@ __device__ __forceinline__ bool grid_barrier(GridBar* b, Ctrl* c, unsigned nbloc
             }
             if (spins > 64) __nanosleep(32);
         }
-        __threadfence();
-        gen = g + 1u;
+        nbar = bn;
+        s_flag = ok ? (int)(word & 1u) : 0;
     }
-    return __syncthreads_and(ok) != 0;
+    ok = __syncthreads_and(ok);
+    *flag = s_flag;
+    return ok != 0;
+}
+
+// W bytes of a canvas row starting at p, realigned into ((W + 3) / 4)
+// words (byte j at bits 8 (j % 4) of word j / 4); reads whole aligned words,
+// which the canvas padding keeps in bounds.
+template <int W>
+__device__ __forceinline__ void load_row_bytes(const uint8_t* p, uint32_t (&r)[(W + 3) / 4]) {
+    constexpr int NW = (W + 3) / 4;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(p);
+    const uint32_t* q = reinterpret_cast<const uint32_t*>(a & ~uintptr_t(3));
+    const uint32_t sh = (uint32_t)(a & 3u) * 8u;
+    uint32_t w[NW + 1];
+#pragma unroll
+    for (int i = 0; i <= NW; ++i) w[i] = __ldcg(q + i);
+#pragma unroll
+    for (int i = 0; i < NW; ++i) r[i] = __funnelshift_r(w[i], w[i + 1], sh);
 }
 
 }  // namespace
@@ -112,7 +142,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
     constexpr int kWarps = kListThreads / 32;
     __shared__ int s_np;
     __shared__ unsigned s_k, s_cur, s_aux, s_maxk, s_gen;
-    __shared__ unsigned s_n, s_nclr, s_changed;
+    __shared__ unsigned s_n, s_nclr;
     __shared__ uint32_t stage_all[kWarps][StagedList::kCap];
     __shared__ int s_counts[kWarps + 1];
     __shared__ unsigned long long s_evals;
@@ -125,7 +155,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
         s_cur = __ldcg(&ctrl->cur);
         s_aux = __ldcg(&ctrl->aux);
         s_maxk = __ldcg(&ctrl->max_k);
-        s_gen = 0u;  // the barrier struct is zeroed at the start of every call
+        s_gen = 0u;  // barriers completed; the barrier struct is zeroed at the start of every call
     }
     __syncthreads();
     if (s_np == 0) return;  // the fused launch already finished the call
@@ -155,7 +185,6 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
                 // Set (t + 2) % 4 is next written by pass t + 1; its list was
                 // last read (to clear its bitmap) in pass t - 1.
                 ctrl->list_n[(t + 2) & 3] = 0u;
-                ctrl->changed[(t + 1) % 3] = 0u;
             }
         }
         __syncthreads();
@@ -194,15 +223,21 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
                     const int py = (int)(pk >> 16), px = (int)(pk & 0xffffu);
                     const int y = py + dy, x = px + dx;
                     if (y >= B && y < a.rows - B && x >= B && x < a.cols - B) {
-                        // Ownership: no changed pixel of q's window precedes p
-                        // in raster order (rows above p's, then p's row left
-                        // of p).  All bitmap rows are loaded before testing.
+                        // Issue every load first: the bitmap rows of q's
+                        // window up to p's row, and q's window itself.
                         uint32_t rb[2 * B + 1];
 #pragma unroll
                         for (int r = 0; r <= 2 * B; ++r) {
                             const int gy = y - B + r;
                             rb[r] = (gy <= py) ? row_bits(bm_prev + (size_t)gy * a.bm_words, a.bm_words, x - B) : 0u;
                         }
+                        constexpr int NW = (W + 3) / 4;
+                        uint32_t win[W][NW];
+                        const long long off = (long long)y * a.pitch + x;
+#pragma unroll
+                        for (int r = 0; r < W; ++r) load_row_bytes<W>(in + off + (long long)(r - B) * a.pitch - B, win[r]);
+                        // Ownership: no changed pixel of q's window precedes p
+                        // in raster order (rows above p's, then p's row left of p).
                         bool owner = true;
 #pragma unroll
                         for (int r = 0; r <= 2 * B; ++r) {
@@ -212,9 +247,23 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
                         }
                         if (owner) {
                             ++evals;
-                            const long long off = (long long)y * a.pitch + x;
-                            const int ip = in[off];
-                            const int nv = eval_pixel<B>(in + off, a.pitch, a.alpha);
+                            // Algorithm 2 on the loaded window (see eval_pixel).
+                            const int ip = (int)((win[B][B / 4] >> (8 * (B % 4))) & 0xffu);
+                            int sum = 0, flag = 0;
+#pragma unroll
+                            for (int r = 0; r < W; ++r)
+#pragma unroll
+                                for (int j = 0; j < W; ++j) {
+                                    const int tv = (int)((win[r][j / 4] >> (8 * (j % 4))) & 0xffu);
+                                    const bool open = !(tv < ip + a.alpha + 1 && tv > ip - a.alpha);
+                                    sum += open ? tv * tv : 0;
+                                    flag += open ? 1 : 0;
+                                }
+                            int nv = ip;
+                            if (flag > P - 3) {
+                                const float qf = floorf(__fdiv_rn((float)sum, (float)flag));
+                                nv = (int)floorf(__fsqrt_rn(qf));
+                            }
                             out[off] = (uint8_t)nv;
                             if (nv != ip) {
                                 ch = true;
@@ -255,15 +304,13 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
             }
         }
         staged_flush(sl, next, nnext, a.list_cap, s_counts, kWarps);
-        if (__syncthreads_or(any) && tid == 0) ctrl->changed[t % 3] = 1u;
         ++passes;
-        if (!grid_barrier(a.bar, ctrl, gridDim.x, gen)) {
+        int changed = any ? 1 : 0;
+        if (!grid_barrier(a.bar, ctrl, gridDim.x, gen, &changed)) {
             failed = true;
             break;
         }
-        if (tid == 0) s_changed = __ldcg(&ctrl->changed[t % 3]);
-        __syncthreads();
-        if (!s_changed) {
+        if (!changed) {
             converged = true;  // a fixed point: the output canvas equals the input
             break;
         }

@@ -94,7 +94,6 @@ __global__ void ctrl_init_kernel(Ctrl* c, unsigned max_k) {
     c->work_launches = 0;
     c->executed = 0;
     for (int i = 0; i < 4; ++i) c->list_n[i] = 0;
-    for (int i = 0; i < 3; ++i) c->changed[i] = 0;
     c->error = 0;
     c->evals_fused = 0;
     c->evals_list = 0;
