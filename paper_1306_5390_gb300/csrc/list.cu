@@ -66,10 +66,6 @@ __device__ __forceinline__ int eval_pixel(const uint8_t* p, long long stride, in
     return ip;
 }
 
-__device__ __forceinline__ void store_release(unsigned* p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-
 // Grid-wide barrier over co-resident CTAs (see GridBar) that also ORs one
 // flag over all CTAs.  Arrival counts sit in the low 16 bits of the group and
 // root counters and flag counts in the high bits; the release word of
@@ -95,13 +91,13 @@ __device__ __forceinline__ bool grid_barrier(GridBar* b, Ctrl* c, unsigned nbloc
             if ((orr & 0xffffu) == ng - 1u) {
                 const unsigned all = ((orr >> 16) + gflag) ? 1u : 0u;
                 b->root.v = 0u;
-                __threadfence();
-                for (unsigned j = 0; j < ng; ++j) store_release(&b->gen[j].v, 2u * bn + all);
+                __threadfence();  // orders every release below after all prior writes
+                for (unsigned j = 0; j < ng; ++j) *reinterpret_cast<volatile unsigned*>(&b->gen[j].v) = 2u * bn + all;
             }
         }
         unsigned spins = 0, word = 0;
         while (true) {
-            asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(word) : "l"(&b->gen[grp].v) : "memory");
+            word = *reinterpret_cast<volatile const unsigned*>(&b->gen[grp].v);
             if ((word >> 1) == bn) break;
             if (++spins > (1u << 22)) {  // one to two seconds
                 atomicExch(&c->error, 1u);
@@ -110,6 +106,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar* b, Ctrl* c, unsigned nbloc
             }
             if (spins > 64) __nanosleep(32);
         }
+        __threadfence();  // later reads see every write released by the barrier
         nbar = bn;
         s_flag = ok ? (int)(word & 1u) : 0;
     }
