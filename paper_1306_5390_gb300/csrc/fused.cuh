@@ -54,11 +54,14 @@ namespace hg {
 
 template <int B, int T>
 struct FusedGeo {
-    static constexpr int kThreads = 256;
+    // beta 1 uses 16 warps of 4-row bands (twice the resident warps at the
+    // same shared memory); wider windows need more registers per thread and
+    // use 8 warps of 8-row bands.
+    static constexpr int kThreads = B == 1 ? 512 : 256;
     static constexpr int kWarps = kThreads / 32;
-    static constexpr int kRows = 8;                  // rows per warp band (dense passes)
+    static constexpr int RN = 64;                    // rows computed per pass
+    static constexpr int kRows = RN / kWarps;        // rows per warp band (dense passes)
     static constexpr int TW = 240;                   // core tile width (pixels)
-    static constexpr int RN = kRows * kWarps;        // rows computed per pass (64)
     static constexpr int TH = RN - 2 * (T - 1) * B;  // core tile height
     static constexpr int H = T * B;                  // vertical halo
     static constexpr int SH = TH + 2 * H;            // tile rows in shared memory (= RN + 2B)
@@ -68,7 +71,7 @@ struct FusedGeo {
     static constexpr int C0 = kPadX - 8;             // first computed column
     static constexpr int CN = 256;                   // computed columns
     static constexpr int P = (2 * B + 1) * (2 * B + 1);
-    static constexpr int kCandCap = 1024;            // per-warp candidate list (half a band)
+    static constexpr int kCandCap = kRows / 2 * 256;  // per-warp candidate list (half a band)
     static constexpr int kListCap = 2048;            // changed pixels kept per pass
     static constexpr int kListEvalMax = 2048;        // list-pass evaluations above which a pass runs dense
     static constexpr int kMarkWords = (SH * SW + 31) / 32;
@@ -352,8 +355,10 @@ __device__ __forceinline__ void band_dense(PassCtx<B, T>& c, const int ys, const
         if ((all & 0x40004000u) != 0x40004000u)
             m64 |= (unsigned long long)candidate_mask(cnt) << (8 * r);
     }
-    append_bits<B, T>(c, lane, (uint32_t)m64, ys, 2 * ws);
-    append_bits<B, T>(c, lane, (uint32_t)(m64 >> 32), ys + 4, 2 * ws);
+    constexpr int kHalf = G::kRows / 2;  // rows per append (a half band fits the list)
+    constexpr unsigned long long kHalfMask = (1ull << (8 * kHalf)) - 1ull;
+    append_bits<B, T>(c, lane, (uint32_t)(m64 & kHalfMask), ys, 2 * ws);
+    append_bits<B, T>(c, lane, (uint32_t)((m64 >> (8 * kHalf)) & kHalfMask), ys + kHalf, 2 * ws);
 }
 
 // List pass: only pixels within beta of a pixel that changed in the
@@ -396,7 +401,7 @@ __device__ __forceinline__ void list_pass(PassCtx<B, T>& c, const uint16_t* prev
 }
 
 template <int B, int T>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(FusedGeo<B, T>::kThreads, 2)
 fused_kernel(PassArgs a) {
     using G = FusedGeo<B, T>;
     extern __shared__ __align__(16) uint8_t smem[];
