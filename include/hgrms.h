@@ -51,6 +51,7 @@ extern "C" {
 #define HGRMS_ECUDA    (-3) /* a CUDA runtime call or kernel failed; see hgrms_last_cuda_error */
 #define HGRMS_ETIMEOUT (-4) /* a bounded device wait gave up */
 #define HGRMS_ENODEV   (-5) /* no CUDA device, or the device index is out of range */
+#define HGRMS_ETOOBIG  (-6) /* image too large for hgrms_denoise_noalloc's fixed scratch */
 
 typedef struct hgrms_ctx* hgrms_t;
 
@@ -91,6 +92,38 @@ const char* hgrms_strerror(int code);
 
 /* The cudaError_t of the last failing CUDA call on this handle (0 if none). */
 int hgrms_last_cuda_error(hgrms_t h);
+
+/* ---- Denoising without device allocation ------------------------------- */
+
+/* Bytes of the fixed device scratch array behind hgrms_denoise_noalloc. */
+#define HGRMS_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* The same denoising as hgrms_denoise (fused tile kernel, repeated fused
+ * launches), for callers that must not allocate device memory: code whose
+ * device memory is owned by a pool or host application it cannot bypass,
+ * and latency-critical paths where an allocation may stall or fail.  No
+ * handle is needed and the call makes no cudaMalloc/cudaFree (nor any other
+ * allocating call): every scratch buffer lives in one file-scope __device__
+ * array of HGRMS_NOALLOC_SCRATCH_BYTES that each GPU loading the library
+ * keeps until the process exits.  The paper has no counterpart; this is an
+ * interface of this library only.
+ *
+ *   img       device memory of the current CUDA device, rows x cols dense,
+ *             denoised in place (host memory is rejected with HGRMS_EINVAL).
+ *   cuda_stream  a cudaStream_t, or NULL for the default stream; the call
+ *             returns after the work on it finished.
+ * Returns k (as hgrms_denoise) or a negative code; HGRMS_ETOOBIG when the
+ * scratch the image needs exceeds the array (images with rows, cols <= 2048
+ * always fit; larger ones fit while their two padded canvases and change
+ * bitmaps do).  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) and may load the library's device code:
+ * make that first call before capturing any stream into a CUDA graph.  All
+ * calls on a device share the array (it keeps the last call's contents;
+ * each call re-initialises what it reads), so calls whose GPU work overlaps
+ * - from two streams or two host threads - race and must be serialised by
+ * the caller. */
+int hgrms_denoise_noalloc(uint8_t* img, int rows, int cols, int alpha, int beta, int max_k,
+                          void* cuda_stream);
 
 /* ---- Tuning and measurement (not part of the method) ------------------ */
 

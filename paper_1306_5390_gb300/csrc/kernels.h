@@ -15,6 +15,11 @@ extern const int kFusedB2Count;
 extern const FusedEntry kFusedB3[];
 extern const int kFusedB3Count;
 
+// Compiled fused kernel for (beta, passes per launch), or null; the built-in
+// passes per launch for beta.
+const FusedEntry* find_fused(int beta, int T);
+int default_passes(int beta);
+
 cudaError_t launch_plain(int beta, const PassArgs& a, cudaStream_t s);
 cudaError_t launch_ctrl_init(Ctrl* c, unsigned max_k, cudaStream_t s);
 cudaError_t launch_copy_in(const uint8_t* img, int rows, int cols, uint8_t* canvas, long long pitch,

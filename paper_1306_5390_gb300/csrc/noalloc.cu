@@ -1,0 +1,134 @@
+// hgrms_denoise_noalloc: the fused tile path for callers that cannot
+// allocate device memory.
+//
+// Some callers must not call cudaMalloc or cudaFree at all: code running
+// under a memory pool or arena they do not control, real-time or
+// latency-critical paths where an allocation can stall or fail, and plug-ins
+// embedded in hosts that own the device's memory.  This entry point takes
+// every piece of scratch memory (two image canvases, the change bitmaps the
+// launches pass to each other and the control block) from one file-scope
+// __device__ array of fixed size, so a call allocates nothing; the caller
+// passes the image (device memory) and gets it back denoised in place.
+//
+// The array is part of the library's device image: every GPU on which the
+// library is loaded holds it until the process exits.  Host code cannot use
+// the array's name as a device address, so the first call on each device
+// asks the runtime for the address (cudaGetSymbolAddress, with that device
+// current) and caches it.
+#include <mutex>
+
+#include "../../include/hgrms.h"
+#include "fused.cuh"
+#include "kernels.h"
+
+namespace {
+
+constexpr size_t kScratchBytes = (size_t)HGRMS_NOALLOC_SCRATCH_BYTES;
+__device__ __align__(256) uint8_t g_noalloc_scratch[kScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+uint8_t* g_scratch_addr[kMaxDevices] = {};
+
+// Device address of the array on `device` (current), looked up once.
+cudaError_t scratch_address(int device, uint8_t** out) {
+    std::lock_guard<std::mutex> lock(g_mu);
+    if (!g_scratch_addr[device]) {
+        void* p = nullptr;
+        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_scratch_addr[device] = static_cast<uint8_t*>(p);
+    }
+    *out = g_scratch_addr[device];
+    return cudaSuccess;
+}
+
+size_t align256(size_t n) { return (n + 255) / 256 * 256; }
+
+int fail(cudaError_t e) {
+    return e == cudaErrorMemoryAllocation ? HGRMS_ENOMEM : HGRMS_ECUDA;
+}
+
+}  // namespace
+
+#define HG_NA_TRY(call)                            \
+    do {                                           \
+        const cudaError_t e_ = (call);             \
+        if (e_ != cudaSuccess) return fail(e_);    \
+    } while (0)
+
+extern "C" __attribute__((visibility("default"))) int hgrms_denoise_noalloc(uint8_t* img, int rows, int cols,
+                                                                           int alpha, int beta, int max_k,
+                                                                           void* cuda_stream) {
+    if (!img || rows < 1 || cols < 1 || rows > 65536 || cols > 65536) return HGRMS_EINVAL;
+    if (alpha < 0 || alpha > 255 || beta < 1 || beta > hg::kMaxBeta || max_k < 0 || max_k > 1000000)
+        return HGRMS_EINVAL;
+    int device = 0;
+    HG_NA_TRY(cudaGetDevice(&device));
+    if (device < 0 || device >= kMaxDevices) return HGRMS_ENODEV;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, img) != cudaSuccess) {
+        cudaGetLastError();
+        return HGRMS_EINVAL;
+    }
+    if ((at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged) || at.device != device)
+        return HGRMS_EINVAL;  // device memory of the current device only
+
+    // Geometry of the fused kernel (fused tile launches only).
+    const int T = hg::default_passes(beta);
+    const hg::FusedEntry* fe = hg::find_fused(beta, T);
+    if (!fe) return HGRMS_EINVAL;
+    const int tiles_x = (cols + fe->TW - 1) / fe->TW;
+    const int tiles_y = (rows + fe->TH - 1) / fe->TH;
+    const long long pitch = (hg::kPadX + (long long)tiles_x * fe->TW + 16 + 127) / 128 * 128;
+    const long long crows = hg::kPadY + (long long)tiles_y * fe->TH + 16;
+    const int map_words = (tiles_x * fe->TW + 31) / 32 + 2;
+    const size_t ctrl_bytes = align256(sizeof(hg::Ctrl));
+    const size_t canvas_bytes = align256((size_t)(pitch * crows));
+    const size_t map_bytes = (size_t)rows * (size_t)map_words * sizeof(uint32_t);
+    const size_t need = ctrl_bytes + 2 * canvas_bytes + align256(3 * map_bytes);
+    if (need > kScratchBytes) return HGRMS_ETOOBIG;
+
+    uint8_t* base = nullptr;
+    HG_NA_TRY(scratch_address(device, &base));
+    cudaStream_t s = (cudaStream_t)cuda_stream;
+    int sms = 0;
+    HG_NA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+
+    hg::Ctrl* ctrl = reinterpret_cast<hg::Ctrl*>(base);
+    hg::PassArgs a;
+    a.canvas[0] = base + ctrl_bytes;
+    a.canvas[1] = a.canvas[0] + canvas_bytes;
+    a.canvas[2] = a.canvas[0];  // the third canvas is only written for list passes, which this path has not
+    a.pitch = pitch;
+    a.rows = rows;
+    a.cols = cols;
+    a.alpha = alpha;
+    a.tiles_x = tiles_x;
+    a.ctrl = ctrl;
+    a.chg_maps = reinterpret_cast<uint32_t*>(a.canvas[1] + canvas_bytes);
+    a.map_words = map_words;
+    for (int i = 0; i < 4; ++i) {
+        a.lists[i] = nullptr;
+        a.bitmaps[i] = nullptr;
+    }
+    a.list_cap = 0;
+    a.bm_words = 0;
+    a.write_prev = 0;
+    a.bar = nullptr;
+
+    // The array keeps the previous call's contents: the control block is
+    // reset by ctrl_init and change map 0 (written by the first launch) is
+    // cleared here; the launches clear the other maps themselves.  Canvas
+    // bytes outside the image are never read by a pixel that can change.
+    HG_NA_TRY(hg::launch_copy_in(img, rows, cols, a.canvas[0], pitch, sms, s));
+    HG_NA_TRY(hg::launch_ctrl_init(ctrl, (unsigned)max_k, s));
+    HG_NA_TRY(cudaMemsetAsync(a.chg_maps, 0, map_bytes, s));
+    const int launches = (max_k + T - 1) / T;
+    for (int i = 0; i < launches; ++i) HG_NA_TRY(fe->launch(a, tiles_y, s));
+    HG_NA_TRY(hg::launch_copy_out(ctrl, a.canvas, pitch, img, rows, cols, sms, s));
+    unsigned k = 0;
+    HG_NA_TRY(cudaMemcpyAsync(&k, &ctrl->k, sizeof(k), cudaMemcpyDeviceToHost, s));
+    HG_NA_TRY(cudaStreamSynchronize(s));
+    return (int)k;
+}

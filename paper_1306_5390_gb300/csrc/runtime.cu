@@ -51,9 +51,9 @@ struct hgrms_ctx {
     std::vector<int> launch_kind;  // 0 = fused, 1 = list pass, 2 = unfused
 };
 
-namespace {
+namespace hg {
 
-const hg::FusedEntry* find_fused(int beta, int T) {
+const FusedEntry* find_fused(int beta, int T) {
     const hg::FusedEntry* tabs[3] = {hg::kFusedB1, hg::kFusedB2, hg::kFusedB3};
     const int counts[3] = {hg::kFusedB1Count, hg::kFusedB2Count, hg::kFusedB3Count};
     for (int t = 0; t < 3; ++t)
@@ -71,6 +71,13 @@ int default_passes(int beta) {
         default: return 1;
     }
 }
+
+}  // namespace hg
+
+namespace {
+
+using hg::default_passes;
+using hg::find_fused;
 
 int cuda_fail(hgrms_ctx* h, cudaError_t e) {
     h->last_cuda_error = (int)e;
@@ -457,6 +464,7 @@ HG_EXPORT const char* hgrms_strerror(int code) {
         case HGRMS_ECUDA: return "CUDA error";
         case HGRMS_ETIMEOUT: return "device wait timed out";
         case HGRMS_ENODEV: return "no CUDA device";
+        case HGRMS_ETOOBIG: return "image too large for the fixed scratch of hgrms_denoise_noalloc";
         default: return code >= 0 ? "success" : "unknown error";
     }
 }

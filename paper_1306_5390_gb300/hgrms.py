@@ -23,6 +23,8 @@ HGRMS_ENOMEM = -2
 HGRMS_ECUDA = -3
 HGRMS_ETIMEOUT = -4
 HGRMS_ENODEV = -5
+HGRMS_ETOOBIG = -6
+HGRMS_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 HGRMS_OPT_KERNEL = 1
 HGRMS_OPT_PASSES = 2
@@ -34,6 +36,7 @@ EXPORTED = (
     "hgrms_create", "hgrms_destroy", "hgrms_denoise", "hgrms_denoise_batch",
     "hgrms_converged", "hgrms_strerror", "hgrms_last_cuda_error", "hgrms_set_option",
     "hgrms_stats", "hgrms_launch_times", "hgrms_default_passes", "hgrms_has_kernel",
+    "hgrms_denoise_noalloc",
 )
 
 
@@ -101,6 +104,8 @@ def load_library(path: str | None = None):
         lib.hgrms_stats.restype = ctypes.c_int
         lib.hgrms_launch_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ip, ctypes.c_int]
         lib.hgrms_launch_times.restype = ctypes.c_int
+        lib.hgrms_denoise_noalloc.argtypes = [vp] + [ctypes.c_int] * 5 + [vp]
+        lib.hgrms_denoise_noalloc.restype = ctypes.c_int
         lib.hgrms_default_passes.argtypes = [ctypes.c_int]
         lib.hgrms_default_passes.restype = ctypes.c_int
         lib.hgrms_has_kernel.argtypes = [ctypes.c_int, ctypes.c_int]
@@ -138,6 +143,12 @@ def hgrms_denoise_batch(h, ptrs, rows, cols, alpha: int, beta: int, max_k: int, 
     for i in range(n):
         k_out[i] = K[i]
     return rc
+
+
+def hgrms_denoise_noalloc(img_ptr: int, rows: int, cols: int, alpha: int, beta: int, max_k: int,
+                          cuda_stream: int | None = None) -> int:
+    """Raw call of the allocation-free entry point: returns k or a negative code."""
+    return load_library().hgrms_denoise_noalloc(img_ptr, rows, cols, alpha, beta, max_k, cuda_stream)
 
 
 def hgrms_converged(h) -> int:
