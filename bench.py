@@ -41,7 +41,7 @@ L2_FLUSH_BYTES = 256 << 20
 def parse_args(argv=None):
     p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
     p.add_argument("--workload", choices=("8192", "256"), default="8192")
@@ -62,6 +62,19 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", str(rank)))
     return rank, world, local
+
+
+def combine_ranks(dist, device, total_s: float, units: int):
+    """Whole-job figures over the ranks: the slowest rank's time and the
+    units all ranks processed."""
+    if dist is None:
+        return total_s, units
+    import torch
+    t = torch.tensor([total_s], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), int(u.item())
 
 
 def measured_peaks():
@@ -104,7 +117,7 @@ class ClockSampler:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "25"],
                 stdout=self.file, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
@@ -214,13 +227,7 @@ def run_ours(args, rank, world, local):
         total_ms += ev0.elapsed_time(ev1)
         units += sum(rows * cols * acc[b]["k"] for b in betas)
     clk = clocks.stop()
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        u = torch.tensor([units], dtype=torch.float64, device="cuda")
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        units = int(u.item())
+    total_ms, units = combine_ranks(dist, "cuda", total_ms, units)
     value = units / (total_ms * 1e-3) / 1e6
 
     # End to end: host (pinned) image in, host image out, through the C ABI.
@@ -237,13 +244,7 @@ def run_ours(args, rank, world, local):
         ks = [d.denoise(host_np[i], alpha, b, max_k) for i, b in enumerate(betas)]
         e2e_s += time.perf_counter() - t0
         e2e_units += sum(rows * cols * k for k in ks)
-    if dist is not None:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-        u = torch.tensor([e2e_units], dtype=torch.float64, device="cuda")
-        dist.all_reduce(u, op=dist.ReduceOp.SUM)
-        e2e_units = int(u.item())
+    e2e_s, e2e_units = combine_ranks(dist, "cuda", e2e_s, e2e_units)
     e2e_value = e2e_units / e2e_s / 1e6 if e2e_s > 0 else None
 
     peaks, peak_kind = measured_peaks()
