@@ -251,7 +251,7 @@ def run_ours(args, rank, world, local):
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = sms * 128 * sm_mhz * 1e6 / 1e9  # Gop/s: one 32-bit op per lane per clock
-    kind_name = {0: "fused_kernel", 1: "list_kernel", 2: "plain_kernel"}
+    kind_name = {0: "fused_kernel", 1: "list_loop_kernel", 2: "plain_kernel"}
     per_beta_out = {}
     kernels = []  # (total ms, name, beta, tests, launches)
     for b in betas:
@@ -328,21 +328,40 @@ def run_ours(args, rank, world, local):
         print(json.dumps(out), flush=True)
 
 
+def kernel_source_hash():
+    """First 16 hex digits of a SHA-256 over the CUDA sources (file names and
+    bytes, in name order); an ncu summary records the hash it was taken on."""
+    import hashlib
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1306_5390_gb300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(f.encode())
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def traffic_from_profiles(name, beta, T, rows, cols):
     """DRAM bytes per launch of the dominant kernel from a committed ncu
     summary (profiles/<kernel>_b<beta>[_t<T>]_<rows>x<cols>.txt, line
-    'dram_bytes_per_launch:'), or None when no capture of it exists."""
+    'dram_bytes_per_launch:'), or None when no capture of it exists or the
+    kernels have changed since it was taken (its 'source_sha256:' differs)."""
     tag = f"{name}_b{beta}" + (f"_t{T}" if name == "fused_kernel" else "")
     path = os.path.join(ROOT, "profiles", f"{tag}_{rows}x{cols}.txt")
     if not os.path.exists(path):
         return None
+    value, sha = None, None
     for ln in open(path):
-        if ln.startswith("dram_bytes_per_launch:"):
+        if "source_sha256:" in ln:
+            sha = ln.split("source_sha256:", 1)[1].split()[0]
+        elif ln.startswith("dram_bytes_per_launch:"):
             try:
-                return int(float(ln.split(":", 1)[1].split()[0]))
+                value = int(float(ln.split(":", 1)[1].split()[0]))
             except ValueError:
                 return None
-    return None
+    if sha != kernel_source_hash():
+        return None
+    return value
 
 
 def oracle_sample(w, band_rows):
