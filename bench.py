@@ -54,6 +54,10 @@ def parse_args(argv=None):
     p.add_argument("--ref-rows", type=int, default=64, help="rows of each reference-arm step")
     p.add_argument("--e2e-steps", type=int, default=3)
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--batch-images", type=int, default=512,
+                   help="images of the uneven-batch comparison (0 = skip it)")
+    p.add_argument("--batch-steps", type=int, default=5)
+    p.add_argument("--loop-steps", type=int, default=2)
     return p.parse_args(argv)
 
 
@@ -318,6 +322,10 @@ def run_ours(args, rank, world, local):
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if args.batch_images > 0:
+        out["batched"] = batch_section(torch, local, args)
+        launches_b = out["batched"].pop("_launches")
+        out["gpu_launches_batched_step"] = launches_b
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, args.cpu_rows)
     d.close()
@@ -339,6 +347,66 @@ def kernel_source_hash():
         with open(os.path.join(d, f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
+
+
+def batch_section(torch, local, args):
+    """The uneven batch (images with sides uniform in 128..2048, impulse
+    density 5..70 %, alpha 10, beta 1, max_k 32), resident on the device:
+    one hgrms_denoise_batch call per step against one hgrms_denoise call per
+    image per step, on the same inputs; the two must give identical bytes and
+    k for every image."""
+    from paper_1306_5390_gb300 import hgrms, synth
+    n = args.batch_images
+    ws = list(synth.workload_batch(512 if n <= 512 else n, last=n))
+    shapes = [w["noisy"].shape for w in ws]
+    sizes = [r * c for r, c in shapes]
+    offs = np.cumsum([0] + sizes)
+    pristine = torch.from_numpy(np.concatenate([w["noisy"].ravel() for w in ws])).cuda()
+    work = torch.empty_like(pristine)
+    views = [work[int(offs[i]):int(offs[i + 1])].view(shapes[i]) for i in range(n)]
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    d = hgrms.Denoiser(local)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, steps, warm):
+        ks = None
+        for _ in range(warm):
+            work.copy_(pristine)
+            fn()
+        tot = 0.0
+        for _ in range(steps):
+            work.copy_(pristine)
+            flush.zero_()
+            torch.cuda.synchronize()
+            ev0.record()
+            ks = fn()
+            ev1.record()
+            torch.cuda.synchronize()
+            tot += ev0.elapsed_time(ev1)
+        return tot / steps, ks
+
+    ms_b, ks_b = timed(lambda: d.denoise_batch(views, 10, 1, 32), args.batch_steps, 1)
+    st = d.stats()
+    out_b = work.clone()
+    ms_l, ks_l = timed(lambda: [d.denoise(v, 10, 1, 32) for v in views], args.loop_steps, 1)
+    same = bool(torch.equal(work, out_b)) and list(ks_b) == list(ks_l)
+    d.close()
+    pix_iters = sum(s_ * k for s_, k in zip(sizes, ks_b))
+    return {
+        "workload": f"{n} uint8 images, sides uniform 128..2048, salt-and-pepper 5..70%, alpha 10, beta 1, max_k 32",
+        "pixels": int(offs[-1]),
+        "k_mean": round(float(np.mean(ks_b)), 3), "k_max": int(max(ks_b)),
+        "batched": {"ms_per_step": round(ms_b, 3), "images_per_s": round(n / (ms_b * 1e-3), 1),
+                    "mpix_iter_per_s": round(pix_iters / (ms_b * 1e-3) / 1e6, 1), "steps": args.batch_steps},
+        "per_image_loop": {"ms_per_step": round(ms_l, 3), "images_per_s": round(n / (ms_l * 1e-3), 1),
+                           "mpix_iter_per_s": round(pix_iters / (ms_l * 1e-3) / 1e6, 1), "steps": args.loop_steps},
+        "speedup": round(ms_l / ms_b, 3),
+        "identical_outputs_and_k": same,
+        "l2": f"{L2_FLUSH_BYTES >> 20} MiB buffer written before every timed step",
+        # copies in and out, table upload, tile map, control init, fused, list loop
+        "_launches": int(st["launches"]) + 4,
+    }
 
 
 def traffic_from_profiles(name, beta, T, rows, cols):

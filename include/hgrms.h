@@ -74,10 +74,17 @@ void hgrms_destroy(hgrms_t h);
 int hgrms_denoise(hgrms_t h, uint8_t* img, int rows, int cols,
                   int alpha, int beta, int max_k);
 
-/* Denoise n independent images with the same alpha, beta and max_k.
- * imgs[i] has rows[i] x cols[i] pixels (all device pointers or all host
- * pointers).  k_out[i] receives image i's k.  Returns HGRMS_OK or a negative
- * code; arguments are validated for every image before any work starts. */
+/* Denoise n independent images with the same alpha, beta and max_k, in
+ * place.  imgs[i] has rows[i] x cols[i] pixels (all device pointers or all
+ * host pointers).  k_out[i] receives image i's k, exactly what
+ * hgrms_denoise returns for that image alone; image i converged (a further
+ * pass would change nothing) exactly when k_out[i] < max_k.  With the
+ * default schedule the images are denoised together: one fused launch over
+ * the tiles of every image, then one persistent launch that runs the
+ * remaining passes for all of them (see HGRMS_OPT_BATCH_MB for how large
+ * batches are split).  Returns HGRMS_OK or a negative code; arguments are
+ * validated for every image before any work starts.  hgrms_converged() then
+ * reports whether every image converged. */
 int hgrms_denoise_batch(hgrms_t h, uint8_t* const* imgs, const int* rows,
                         const int* cols, int n, int alpha, int beta, int max_k,
                         int* k_out);
@@ -135,6 +142,9 @@ int hgrms_denoise_noalloc(uint8_t* img, int rows, int cols, int alpha, int beta,
 #define HGRMS_OPT_TIMING   3 /* 1 = time every denoising launch with CUDA events (see hgrms_stats) */
 #define HGRMS_OPT_LIST_CAP 4 /* capacity of the change lists of list passes (0 = rows*cols/4 + 65536);
                                 when a pass changes more pixels, the next pass evaluates every pixel */
+#define HGRMS_OPT_BATCH_MB 5 /* hgrms_denoise_batch: device memory (MiB) one batched launch may use for
+                                canvases, change lists and bitmaps (0 = 8192); larger batches run as
+                                several chunks of consecutive images, with identical results */
 
 /* Set an option.  Returns HGRMS_OK or HGRMS_EINVAL (unknown option or value,
  * e.g. a pass count that has no compiled kernel for some beta is rejected at

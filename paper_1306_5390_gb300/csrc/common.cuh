@@ -6,6 +6,7 @@
 
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 namespace hg {
 
@@ -15,6 +16,7 @@ namespace hg {
 constexpr int kPadX = 16;   // bytes left of the image; keeps rows 16-byte aligned
 constexpr int kPadY = 16;   // rows above the image (>= any vertical tile halo)
 constexpr int kMaxBeta = 7;
+constexpr int kMaxBatchImages = 4096;  // images per batched launch (more are split into chunks)
 
 // Iteration state shared by the launches of one denoising call.
 //
@@ -57,6 +59,43 @@ struct GridBar {
     BarLine gen[kBarGroups];
 };
 
+// One image of a batch.  The images' canvases are laid out one after another
+// in each of the three canvas arenas (image i's canvas starts `off` bytes into
+// every arena) and their change bitmaps one after another in each bitmap
+// arena (at word `bm_off`).  A single-image call uses a table of one entry.
+struct alignas(16) ImgDesc {
+    long long off;        // canvas offset in each arena (multiple of 128)
+    long long bm_off;     // bitmap offset in words
+    int pitch;            // canvas row pitch (multiple of 128)
+    int rows, cols;
+    int tiles_x;          // fused-kernel tile grid width
+    int tile0;            // first fused-kernel tile of this image
+    int bm_words;         // bitmap words per image row
+    uint8_t* user;        // the caller's image (device memory) for the batched copies, or null
+};
+
+// A change-list entry packs (image, row, column) into 32 bits: the column in
+// the low xb bits, the row in the next yb bits, the image above them (a
+// single image uses xb = yb = 16).
+__device__ __forceinline__ uint32_t pack_entry(unsigned img, int y, int x, int xb, int yb) {
+    return (uint32_t)((unsigned long long)img << (xb + yb)) | ((uint32_t)y << xb) | (uint32_t)x;
+}
+__device__ __forceinline__ void unpack_entry(uint32_t e, int xb, int yb, unsigned& img, int& y, int& x) {
+    x = (int)(e & ((1u << xb) - 1u));
+    y = (int)((e >> xb) & ((1u << yb) - 1u));
+    img = (unsigned)((unsigned long long)e >> (xb + yb));
+}
+
+// The table entry of image i, through the read-only data path.
+__device__ __forceinline__ ImgDesc load_desc(const ImgDesc* t, unsigned i) {
+    static_assert(sizeof(ImgDesc) == 48, "ImgDesc layout");
+    const int4* p = reinterpret_cast<const int4*>(t + i);
+    int4 v[3] = {__ldg(p), __ldg(p + 1), __ldg(p + 2)};
+    ImgDesc d;
+    memcpy(&d, v, sizeof(d));
+    return d;
+}
+
 struct PassArgs {
     uint8_t* canvas[3];       // canvas base pointers (row 0, column 0 of each canvas)
     long long pitch;          // canvas row pitch in bytes (multiple of 16)
@@ -72,7 +111,7 @@ struct PassArgs {
     uint32_t* chg_maps;
     int map_words;            // words per image row
     // Change lists and bitmaps (list passes): changed pixels are appended,
-    // packed as (row << 16) | column, to a list (length ctrl->list_n[i]) and
+    // packed by pack_entry, to a list (length ctrl->list_n[i]) and
     // set in the matching bitmap (rows x bm_words 32-bit words, bit c & 31 of
     // word c >> 5 of row r).  The fused launch writes set 0 with its last
     // pass; list pass t of the list-pass loop reads set t % 4, writes set
@@ -83,6 +122,19 @@ struct PassArgs {
     int bm_words;
     int write_prev;           // fused kernel: also write I_{t-1} to the third canvas
     GridBar* bar;             // list-pass loop barrier
+    // Image table (hybrid schedule: fused launch + list-pass loop).  When
+    // set, the fields above that describe one image (pitch, rows, cols,
+    // tiles_x, bm_words) are unused: canvases and bitmaps are arenas, fused
+    // tile b belongs to image tile_img[b], and list entries are packed with
+    // (xb, yb).  img_k[i], when set, receives image i's k: the number of the
+    // last pass that changed one of its pixels (all images run the same
+    // passes, and an image that a pass leaves unchanged is at a fixed point).
+    const ImgDesc* imgs;
+    int nimg;
+    int xb, yb;
+    const int* tile_img;
+    long long bm_total;       // words in one bitmap arena
+    unsigned* img_k;
 };
 
 // Passes the launch must run: 0 when the call has finished.

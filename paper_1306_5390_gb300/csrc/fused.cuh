@@ -406,7 +406,8 @@ fused_kernel(PassArgs a) {
     using G = FusedGeo<B, T>;
     extern __shared__ __align__(16) uint8_t smem[];
     __shared__ int s_np;
-    __shared__ unsigned s_cur, s_aux, s_launch;
+    __shared__ unsigned s_cur, s_aux, s_launch, s_k, s_img;
+    __shared__ ImgDesc s_d;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     if (tid == 0) {
@@ -414,16 +415,41 @@ fused_kernel(PassArgs a) {
         s_cur = __ldcg(&a.ctrl->cur);
         s_aux = __ldcg(&a.ctrl->aux);
         s_launch = __ldcg(&a.ctrl->work_launches);
+        s_k = __ldcg(&a.ctrl->k);
+        // This tile's image: from the image table, else the single image
+        // described by the arguments.
+        ImgDesc d;
+        unsigned img = 0;
+        if (a.imgs) {
+            img = (unsigned)__ldg(a.tile_img + blockIdx.x);
+            d = load_desc(a.imgs, img);
+        } else {
+            d.off = 0;
+            d.bm_off = 0;
+            d.pitch = (int)a.pitch;
+            d.rows = a.rows;
+            d.cols = a.cols;
+            d.tiles_x = a.tiles_x;
+            d.tile0 = 0;
+            d.bm_words = a.bm_words;
+            d.user = nullptr;
+        }
+        s_d = d;
+        s_img = img;
     }
     __syncthreads();
     const int np = s_np;
     if (np == 0) return;
     const unsigned L = s_launch;
     const unsigned cur = s_cur, aux = s_aux, third = 3u - s_cur - s_aux;
-    const uint8_t* src = a.canvas[cur];
-    uint8_t* dst = a.canvas[aux];
-    const int tx = blockIdx.x % a.tiles_x;
-    const int ty = blockIdx.x / a.tiles_x;
+    const unsigned img = s_img;
+    const long long pitch = s_d.pitch, coff = s_d.off, bm_off = s_d.bm_off;
+    const int rows = s_d.rows, cols = s_d.cols, bm_words = s_d.bm_words;
+    const uint8_t* src = a.canvas[cur] + coff;
+    uint8_t* dst = a.canvas[aux] + coff;
+    const int tile = (int)blockIdx.x - s_d.tile0;
+    const int tx = tile % s_d.tiles_x;
+    const int ty = tile / s_d.tiles_x;
     const int x0 = tx * G::TW, y0 = ty * G::TH;
     uint32_t* buf0 = reinterpret_cast<uint32_t*>(smem);
     uint32_t* buf1 = reinterpret_cast<uint32_t*>(smem + G::kBufBytes);
@@ -432,7 +458,7 @@ fused_kernel(PassArgs a) {
     uint32_t* marks = reinterpret_cast<uint32_t*>(smem + G::kMarkOff);  // 2 bitmaps: pass t uses t & 1
     int* s_cnt = reinterpret_cast<int*>(smem + G::kCntOff);             // list counters, pass t uses t % 3
     const bool use_maps = a.chg_maps != nullptr;
-    const size_t map_size = use_maps ? (size_t)a.rows * (size_t)a.map_words : 0;
+    const size_t map_size = use_maps ? (size_t)rows * (size_t)a.map_words : 0;
     uint32_t* map_out = use_maps ? a.chg_maps + (size_t)(L % 3u) * map_size : nullptr;
     const uint32_t* map_in = use_maps ? a.chg_maps + (size_t)((L + 2u) % 3u) * map_size : nullptr;
     uint32_t* map_clr = use_maps ? a.chg_maps + (size_t)((L + 1u) % 3u) * map_size : nullptr;
@@ -442,11 +468,11 @@ fused_kernel(PassArgs a) {
     // both buffers (a list pass leaves unevaluated pixels as they are in its
     // output buffer, so that buffer must start equal to the input).
     {
-        const uint8_t* base = src + (long long)(kPadY + y0 - G::H) * a.pitch + x0;
+        const uint8_t* base = src + (long long)(kPadY + y0 - G::H) * pitch + x0;
         constexpr int CH = G::SW / 16;
         for (int i = tid; i < G::SH * CH; i += G::kThreads) {
             const int r = i / CH, cc = i - r * CH;
-            const uint4 v = __ldg(reinterpret_cast<const uint4*>(base + (long long)r * a.pitch + cc * 16));
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(base + (long long)r * pitch + cc * 16));
             uint4 lo, hi;
             lo.x = bytes_to_h2(v.x, 0x4140u); lo.y = bytes_to_h2(v.x, 0x4342u);
             lo.z = bytes_to_h2(v.y, 0x4140u); lo.w = bytes_to_h2(v.y, 0x4342u);
@@ -475,7 +501,7 @@ fused_kernel(PassArgs a) {
         for (int i = tid; i < G::SH * nw; i += G::kThreads) {
             const int y = i / nw, w = wlo + (i - y * nw);
             const int gy = y0 - G::H + y;
-            if (gy < 0 || gy >= a.rows || w < 0 || w >= a.map_words) continue;
+            if (gy < 0 || gy >= rows || w < 0 || w >= a.map_words) continue;
             uint32_t bits = __ldcg(map_in + (size_t)gy * a.map_words + w);
             while (bits) {
                 const int b = __ffs(bits) - 1;
@@ -498,8 +524,8 @@ fused_kernel(PassArgs a) {
     c.ncand = 0;
     c.x0 = x0;
     c.y0 = y0;
-    c.rows = a.rows;
-    c.cols = a.cols;
+    c.rows = rows;
+    c.cols = cols;
     c.alpha = a.alpha;
     c.evals = 0;
     int dense_passes = 0;
@@ -531,9 +557,9 @@ fused_kernel(PassArgs a) {
 
     // Core -> canvas bytes (and I_(np-1) -> the third canvas when asked).
     {
-        const long long off = (long long)(kPadY + y0) * a.pitch + kPadX + x0;
+        const long long off = (long long)(kPadY + y0) * pitch + kPadX + x0;
         uint8_t* base = dst + off;
-        uint8_t* base_prev = a.canvas[third] + off;
+        uint8_t* base_prev = a.canvas[third] + coff + off;
         constexpr int CH = G::TW / 16;
         for (int i = tid; i < G::TH * CH; i += G::kThreads) {
             const int r = i / CH, cc = i - r * CH;
@@ -545,7 +571,7 @@ fused_kernel(PassArgs a) {
             o.y = h2_to_bytes(p.z, p.w);
             o.z = h2_to_bytes(q.x, q.y);
             o.w = h2_to_bytes(q.z, q.w);
-            *reinterpret_cast<uint4*>(base + (long long)r * a.pitch + cc * 16) = o;
+            *reinterpret_cast<uint4*>(base + (long long)r * pitch + cc * 16) = o;
             if (a.write_prev) {
                 const uint4* s2 = reinterpret_cast<const uint4*>(pen + so);
                 const uint4 p2 = s2[0], q2 = s2[1];
@@ -553,7 +579,7 @@ fused_kernel(PassArgs a) {
                 o.y = h2_to_bytes(p2.z, p2.w);
                 o.z = h2_to_bytes(q2.x, q2.y);
                 o.w = h2_to_bytes(q2.z, q2.w);
-                *reinterpret_cast<uint4*>(base_prev + (long long)r * a.pitch + cc * 16) = o;
+                *reinterpret_cast<uint4*>(base_prev + (long long)r * pitch + cc * 16) = o;
             }
         }
     }
@@ -576,9 +602,9 @@ fused_kernel(PassArgs a) {
                 const int q = last[i];
                 const int y = q / G::SW, x = q - y * G::SW;
                 const int gy = y0 + y - G::H, gx = x0 + x - kPadX;
-                if (in_core_px(y, x, G::H, G::TH, G::TW) && gy < a.rows && gx < a.cols) {
-                    sel[atomicAdd(&s_sel[0], 1)] = ((uint32_t)gy << 16) | (uint32_t)gx;
-                    atomicOr(gbm + (size_t)gy * a.bm_words + (gx >> 5), 1u << (gx & 31));
+                if (in_core_px(y, x, G::H, G::TH, G::TW) && gy < rows && gx < cols) {
+                    sel[atomicAdd(&s_sel[0], 1)] = pack_entry(img, gy, gx, a.xb, a.yb);
+                    atomicOr(gbm + bm_off + (size_t)gy * bm_words + (gx >> 5), 1u << (gx & 31));
                 }
             }
             __syncthreads();
@@ -601,13 +627,13 @@ fused_kernel(PassArgs a) {
                 const int y = q / G::SW, x = q - y * G::SW;
                 if (!in_core_px(y, x, G::H, G::TH, G::TW)) continue;
                 const int gy = y0 + y - G::H, gx = x0 + x - kPadX;
-                if (gy >= a.rows || gx >= a.cols) continue;
+                if (gy >= rows || gx >= cols) continue;
                 atomicOr(map_out + (size_t)gy * a.map_words + (gx >> 5), 1u << (gx & 31));
             }
         } else {
             for (int r = tid; r < G::TH; r += G::kThreads) {
                 const int gy = y0 + r;
-                if (gy >= a.rows) break;
+                if (gy >= rows) break;
                 uint32_t* row = map_out + (size_t)gy * a.map_words;
                 for (int gx = x0; gx < x0 + G::TW; gx += 32 - (gx & 31)) {
                     const int n = min(32 - (gx & 31), x0 + G::TW - gx);
@@ -627,12 +653,14 @@ fused_kernel(PassArgs a) {
         if (lane == 0 && ev) atomicAdd(&s_ev[0], (int)ev);
         __syncthreads();
         if (tid == 0) {
-            const int ch = min(G::TH, a.rows - y0), cw = min(G::TW, a.cols - x0);
+            const int ch = min(G::TH, rows - y0), cw = min(G::TW, cols - x0);
             const unsigned long long total =
                 (unsigned long long)s_ev[0] + (unsigned long long)dense_passes * (unsigned long long)(ch * cw);
             if (total) atomicAdd(&a.ctrl->evals_fused, total);
         }
     }
+    // Image k: the image changed in passes 1 .. (highest set bit of the mask).
+    if (tid == 0 && a.img_k && cta_mask) atomicMax(a.img_k + img, s_k + 32u - (unsigned)__clz(cta_mask));
     if (tid == 0) finish_launch(a.ctrl, cta_mask, np, gridDim.x, aux, a.write_prev ? third : cur);
 }
 
@@ -640,16 +668,16 @@ fused_kernel(PassArgs a) {
 struct FusedEntry {
     int beta, T, TH, TW;
     size_t smem;
-    cudaError_t (*launch)(const PassArgs&, int tiles_y, cudaStream_t);
+    cudaError_t (*launch)(const PassArgs&, int ctas, cudaStream_t);  // one CTA per tile
 };
 
 template <int B, int T>
-cudaError_t launch_fused(const PassArgs& a, int tiles_y, cudaStream_t s) {
+cudaError_t launch_fused(const PassArgs& a, int ctas, cudaStream_t s) {
     using G = FusedGeo<B, T>;
     cudaError_t e = cudaFuncSetAttribute(fused_kernel<B, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)G::kSmem);
     if (e != cudaSuccess) return e;
-    fused_kernel<B, T><<<(unsigned)(a.tiles_x * tiles_y), G::kThreads, G::kSmem, s>>>(a);
+    fused_kernel<B, T><<<(unsigned)ctas, G::kThreads, G::kSmem, s>>>(a);
     return cudaGetLastError();
 }
 

@@ -131,9 +131,20 @@ __device__ __forceinline__ void load_row_bytes(const uint8_t* p, uint32_t (&r)[(
     for (int i = 0; i < NW; ++i) r[i] = __funnelshift_r(w[i], w[i + 1], sh);
 }
 
+// Warp-collective: set the bit of `img` in the CTA's changed-image bitmap
+// for every lane with `ch` (one shared atomic per distinct image).
+__device__ __forceinline__ void mark_image(uint32_t* bits, bool ch, unsigned img, int lane) {
+    const unsigned bal = __ballot_sync(0xffffffffu, ch);
+    if (!bal) return;
+    const unsigned peers = __match_any_sync(0xffffffffu, ch ? img : 0xffffffffu);
+    if (ch && (int)(__ffs(peers & bal) - 1) == lane) atomicOr(bits + (img >> 5), 1u << (img & 31));
+}
+
 }  // namespace
 
-template <int B>
+// kBatch = false: one image, described by the launch arguments (pitch, rows,
+// cols, bm_words; entries packed 16/16); true: the image table.
+template <int B, bool kBatch>
 __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) {
     constexpr int W = 2 * B + 1, P = W * W;
     constexpr int kWarps = kListThreads / 32;
@@ -143,6 +154,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
     __shared__ uint32_t stage_all[kWarps][StagedList::kCap];
     __shared__ int s_counts[kWarps + 1];
     __shared__ unsigned long long s_evals;
+    __shared__ uint32_t s_imgbits[kBatch ? kMaxBatchImages / 32 : 1];  // images changed in this pass (by this CTA)
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     Ctrl* ctrl = a.ctrl;
     if (tid == 0) {
@@ -154,6 +166,8 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
         s_maxk = __ldcg(&ctrl->max_k);
         s_gen = 0u;  // barriers completed; the barrier struct is zeroed at the start of every call
     }
+    if constexpr (kBatch)
+        for (int i = tid; i < kMaxBatchImages / 32; i += kListThreads) s_imgbits[i] = 0u;
     __syncthreads();
     if (s_np == 0) return;  // the fused launch already finished the call
     unsigned k = s_k, cur = s_cur, aux = s_aux, gen = s_gen;
@@ -164,12 +178,27 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
     const long long gthreads = (long long)gridDim.x * blockDim.x;
     const long long gtid = (long long)blockIdx.x * blockDim.x + tid;
     const long long warp_base = (long long)blockIdx.x * blockDim.x + (tid & ~31);
+    // The single image as a table entry (its offsets are 0).
+    ImgDesc one;
+    if constexpr (!kBatch) {
+        one.off = 0;
+        one.bm_off = 0;
+        one.pitch = (int)a.pitch;
+        one.rows = a.rows;
+        one.cols = a.cols;
+        one.tiles_x = 0;
+        one.tile0 = 0;
+        one.bm_words = a.bm_words;
+        one.user = nullptr;
+    }
+    constexpr int kXb = 16, kYb = 16;
+    const int xb = kBatch ? a.xb : kXb, yb = kBatch ? a.yb : kYb;
     StagedList sl{stage_all[warp], 0};
 
     for (int t = 0; k < max_k; ++t) {
         const int si = t & 3, so = (t + 1) & 3, sc = (t + 3) & 3;
-        const uint8_t* in = a.canvas[cur] + (long long)kPadY * a.pitch + kPadX;
-        uint8_t* out = a.canvas[aux] + (long long)kPadY * a.pitch + kPadX;
+        const uint8_t* in_arena = a.canvas[cur];
+        uint8_t* out_arena = a.canvas[aux];
         const uint32_t* prev = a.lists[si];
         const uint32_t* bm_prev = a.bitmaps[si];
         uint32_t* next = a.lists[so];
@@ -193,12 +222,14 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
             uint32_t* bm_clr = a.bitmaps[sc];
             if (nclr <= a.list_cap) {
                 for (long long i = gtid; i < nclr; i += gthreads) {
-                    const uint32_t pk = clr[i];
-                    bm_clr[(size_t)(pk >> 16) * a.bm_words + ((pk & 0xffffu) >> 5)] = 0u;
+                    unsigned img;
+                    int y, x;
+                    unpack_entry(clr[i], xb, yb, img, y, x);
+                    const ImgDesc d = kBatch ? load_desc(a.imgs, img) : one;
+                    bm_clr[d.bm_off + (long long)y * d.bm_words + (x >> 5)] = 0u;
                 }
             } else {
-                const size_t words = (size_t)a.rows * a.bm_words;
-                for (size_t i = gtid; i < words; i += gthreads) bm_clr[i] = 0u;
+                for (long long i = gtid; i < a.bm_total; i += gthreads) bm_clr[i] = 0u;
             }
         }
         bool any = false;
@@ -214,25 +245,30 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
                 const uint32_t pk_next = inext < total ? __ldcg(prev + (unsigned)(inext / P)) : 0u;
                 bool ch = false;
                 uint32_t v = 0;
+                unsigned img = 0;
                 if (i < total) {
                     const int o = (int)(i % P);
                     const int dy = o / W - B, dx = o - (o / W) * W - B;
-                    const int py = (int)(pk >> 16), px = (int)(pk & 0xffffu);
+                    int py, px;
+                    unpack_entry(pk, xb, yb, img, py, px);
+                    const ImgDesc d = kBatch ? load_desc(a.imgs, img) : one;
                     const int y = py + dy, x = px + dx;
-                    if (y >= B && y < a.rows - B && x >= B && x < a.cols - B) {
+                    if (y >= B && y < d.rows - B && x >= B && x < d.cols - B) {
+                        const uint32_t* bmp = bm_prev + d.bm_off;
+                        const uint8_t* in = in_arena + d.off + (long long)kPadY * d.pitch + kPadX;
                         // Issue every load first: the bitmap rows of q's
                         // window up to p's row, and q's window itself.
                         uint32_t rb[2 * B + 1];
 #pragma unroll
                         for (int r = 0; r <= 2 * B; ++r) {
                             const int gy = y - B + r;
-                            rb[r] = (gy <= py) ? row_bits(bm_prev + (size_t)gy * a.bm_words, a.bm_words, x - B) : 0u;
+                            rb[r] = (gy <= py) ? row_bits(bmp + (size_t)gy * d.bm_words, d.bm_words, x - B) : 0u;
                         }
                         constexpr int NW = (W + 3) / 4;
                         uint32_t win[W][NW];
-                        const long long off = (long long)y * a.pitch + x;
+                        const long long off = (long long)y * d.pitch + x;
 #pragma unroll
-                        for (int r = 0; r < W; ++r) load_row_bytes<W>(in + off + (long long)(r - B) * a.pitch - B, win[r]);
+                        for (int r = 0; r < W; ++r) load_row_bytes<W>(in + off + (long long)(r - B) * d.pitch - B, win[r]);
                         // Ownership: no changed pixel of q's window precedes p
                         // in raster order (rows above p's, then p's row left of p).
                         bool owner = true;
@@ -261,46 +297,67 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
                                 const float qf = floorf(__fdiv_rn((float)sum, (float)flag));
                                 nv = (int)floorf(__fsqrt_rn(qf));
                             }
-                            out[off] = (uint8_t)nv;
+                            out_arena[d.off + (long long)kPadY * d.pitch + kPadX + off] = (uint8_t)nv;
                             if (nv != ip) {
                                 ch = true;
-                                v = ((uint32_t)y << 16) | (uint32_t)x;
-                                atomicOr(bm_next + (size_t)y * a.bm_words + (x >> 5), 1u << (x & 31));
+                                v = pack_entry(img, y, x, xb, yb);
+                                atomicOr(bm_next + d.bm_off + (size_t)y * d.bm_words + (x >> 5), 1u << (x & 31));
                             }
                         }
                     }
                 }
                 any |= ch;
+                if (kBatch && a.img_k) mark_image(s_imgbits, ch, img, lane);
                 staged_append(sl, next, nnext, a.list_cap, ch, v, lane);
                 pk = pk_next;
             }
         } else {
-            // Previous list overflowed: evaluate and write every pixel.
-            const long long total = (long long)a.rows * a.cols;
-            for (long long base = warp_base; base < total; base += gthreads) {
-                const long long i = base + lane;
-                bool ch = false;
-                uint32_t v = 0;
-                if (i < total) {
-                    const int y = (int)(i / a.cols), x = (int)(i - (long long)y * a.cols);
-                    const long long off = (long long)y * a.pitch + x;
-                    ++evals;
-                    const int ip = in[off];
-                    int nv = ip;
-                    if (y >= B && y < a.rows - B && x >= B && x < a.cols - B)
-                        nv = eval_pixel<B>(in + off, a.pitch, a.alpha);
-                    out[off] = (uint8_t)nv;
-                    if (nv != ip) {
-                        ch = true;
-                        v = ((uint32_t)y << 16) | (uint32_t)x;
-                        atomicOr(bm_next + (size_t)y * a.bm_words + (x >> 5), 1u << (x & 31));
+            // Previous list overflowed: evaluate and write every pixel of
+            // every image.
+            for (int im = 0; im < (kBatch ? a.nimg : 1); ++im) {
+                const ImgDesc d = kBatch ? load_desc(a.imgs, (unsigned)im) : one;
+                const uint8_t* in = in_arena + d.off + (long long)kPadY * d.pitch + kPadX;
+                uint8_t* out = out_arena + d.off + (long long)kPadY * d.pitch + kPadX;
+                const long long total = (long long)d.rows * d.cols;
+                for (long long base = warp_base; base < total; base += gthreads) {
+                    const long long i = base + lane;
+                    bool ch = false;
+                    uint32_t v = 0;
+                    if (i < total) {
+                        const int y = (int)(i / d.cols), x = (int)(i - (long long)y * d.cols);
+                        const long long off = (long long)y * d.pitch + x;
+                        ++evals;
+                        const int ip = in[off];
+                        int nv = ip;
+                        if (y >= B && y < d.rows - B && x >= B && x < d.cols - B)
+                            nv = eval_pixel<B>(in + off, d.pitch, a.alpha);
+                        out[off] = (uint8_t)nv;
+                        if (nv != ip) {
+                            ch = true;
+                            v = pack_entry((unsigned)im, y, x, xb, yb);
+                            atomicOr(bm_next + d.bm_off + (size_t)y * d.bm_words + (x >> 5), 1u << (x & 31));
+                        }
                     }
+                    any |= ch;
+                    if (kBatch && a.img_k) mark_image(s_imgbits, ch, (unsigned)im, lane);
+                    staged_append(sl, next, nnext, a.list_cap, ch, v, lane);
                 }
-                any |= ch;
-                staged_append(sl, next, nnext, a.list_cap, ch, v, lane);
             }
         }
         staged_flush(sl, next, nnext, a.list_cap, s_counts, kWarps);
+        // Images this CTA changed in pass number k + 1 (staged_flush ends
+        // with a block barrier, so every mark is in place).
+        if (kBatch && a.img_k) {
+            for (int w = tid; w < (a.nimg + 31) / 32; w += kListThreads) {
+                uint32_t bits = s_imgbits[w];
+                s_imgbits[w] = 0u;
+                while (bits) {
+                    const int b = __ffs(bits) - 1;
+                    bits &= bits - 1u;
+                    a.img_k[32 * w + b] = k + 1u;
+                }
+            }
+        }
         ++passes;
         int changed = any ? 1 : 0;
         if (!grid_barrier(a.bar, ctrl, gridDim.x, gen, &changed)) {
@@ -336,30 +393,36 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
 
 namespace {
 
-template <int B>
+template <int B, bool kBatch>
 cudaError_t launch_loop_b(const PassArgs& a, int sms, cudaStream_t s) {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, list_loop_kernel<B>, kListThreads, 0);
+    cudaError_t e =
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, list_loop_kernel<B, kBatch>, kListThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const unsigned grid = (unsigned)(sms * (per_sm < 2 ? per_sm : 2));
     PassArgs arg = a;
     void* params[] = {&arg};
-    return cudaLaunchCooperativeKernel((const void*)list_loop_kernel<B>, dim3(grid), dim3(kListThreads), params,
-                                       0, s);
+    return cudaLaunchCooperativeKernel((const void*)list_loop_kernel<B, kBatch>, dim3(grid), dim3(kListThreads),
+                                       params, 0, s);
+}
+
+template <int B>
+cudaError_t launch_loop(const PassArgs& a, int sms, cudaStream_t s) {
+    return a.nimg > 1 ? launch_loop_b<B, true>(a, sms, s) : launch_loop_b<B, false>(a, sms, s);
 }
 
 }  // namespace
 
 cudaError_t launch_list(int beta, const PassArgs& a, int sms, cudaStream_t s) {
     switch (beta) {
-        case 1: return launch_loop_b<1>(a, sms, s);
-        case 2: return launch_loop_b<2>(a, sms, s);
-        case 3: return launch_loop_b<3>(a, sms, s);
-        case 4: return launch_loop_b<4>(a, sms, s);
-        case 5: return launch_loop_b<5>(a, sms, s);
-        case 6: return launch_loop_b<6>(a, sms, s);
-        case 7: return launch_loop_b<7>(a, sms, s);
+        case 1: return launch_loop<1>(a, sms, s);
+        case 2: return launch_loop<2>(a, sms, s);
+        case 3: return launch_loop<3>(a, sms, s);
+        case 4: return launch_loop<4>(a, sms, s);
+        case 5: return launch_loop<5>(a, sms, s);
+        case 6: return launch_loop<6>(a, sms, s);
+        case 7: return launch_loop<7>(a, sms, s);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -116,6 +116,12 @@ extern "C" __attribute__((visibility("default"))) int hgrms_denoise_noalloc(uint
     a.bm_words = 0;
     a.write_prev = 0;
     a.bar = nullptr;
+    a.imgs = nullptr;
+    a.nimg = 1;
+    a.xb = a.yb = 16;
+    a.tile_img = nullptr;
+    a.bm_total = 0;
+    a.img_k = nullptr;
 
     // The array keeps the previous call's contents: the control block is
     // reset by ctrl_init and change map 0 (written by the first launch) is
@@ -125,7 +131,7 @@ extern "C" __attribute__((visibility("default"))) int hgrms_denoise_noalloc(uint
     HG_NA_TRY(hg::launch_ctrl_init(ctrl, (unsigned)max_k, s));
     HG_NA_TRY(cudaMemsetAsync(a.chg_maps, 0, map_bytes, s));
     const int launches = (max_k + T - 1) / T;
-    for (int i = 0; i < launches; ++i) HG_NA_TRY(fe->launch(a, tiles_y, s));
+    for (int i = 0; i < launches; ++i) HG_NA_TRY(fe->launch(a, tiles_x * tiles_y, s));
     HG_NA_TRY(hg::launch_copy_out(ctrl, a.canvas, pitch, img, rows, cols, sms, s));
     unsigned k = 0;
     HG_NA_TRY(cudaMemcpyAsync(&k, &ctrl->k, sizeof(k), cudaMemcpyDeviceToHost, s));

@@ -171,4 +171,112 @@ cudaError_t launch_copy_out(const Ctrl* c, uint8_t* const canvas[3], long long p
     return cudaGetLastError();
 }
 
+// Batched copies: grid (per-image CTAs, images); image blockIdx.y, whose
+// `user` pointer is the caller's dense image (row r at user + r * cols), or
+// null for an image staged by the host.
+
+// Dense image -> canvas: one aligned 4-byte canvas word per thread; the
+// source bytes come from the aligned words that hold them (only words that
+// hold at least one byte of the image are read; the 1..3 bytes a row's last
+// word takes beyond the image land in the canvas's right padding).
+__global__ void copy_in_batch_kernel(const ImgDesc* __restrict__ imgs, uint8_t* __restrict__ arena) {
+    const ImgDesc d = imgs[blockIdx.y];
+    if (!d.user) return;
+    const uint8_t* src = d.user;
+    uint8_t* canvas = arena + d.off + (long long)kPadY * d.pitch + kPadX;
+    const int nwr = (d.cols + 3) / 4;
+    const long long total = (long long)d.rows * nwr;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i / nwr;
+        const int j = (int)(i - r * nwr);
+        const int n = min(4, d.cols - 4 * j);  // image bytes in this word
+        const uintptr_t ad = reinterpret_cast<uintptr_t>(src + r * d.cols + 4 * j);
+        const uint32_t* q = reinterpret_cast<const uint32_t*>(ad & ~uintptr_t(3));
+        const uint32_t sh = (uint32_t)(ad & 3u);
+        const uint32_t w0 = __ldg(q);
+        const uint32_t w1 = (sh != 0u && (int)sh + n > 4) ? __ldg(q + 1) : 0u;
+        *reinterpret_cast<uint32_t*>(canvas + r * d.pitch + 4 * j) = __funnelshift_r(w0, w1, 8u * sh);
+    }
+}
+
+// Canvas `cur` -> dense image: one aligned 4-byte word of the destination
+// per thread, gathered from the canvas; the partial words at the two ends of
+// the image are written byte by byte.
+__global__ void copy_out_batch_kernel(const Ctrl* __restrict__ c, const uint8_t* __restrict__ a0,
+                                      const uint8_t* __restrict__ a1, const uint8_t* __restrict__ a2,
+                                      const ImgDesc* __restrict__ imgs) {
+    const ImgDesc d = imgs[blockIdx.y];
+    if (!d.user) return;
+    const unsigned cur = __ldcg(&c->cur);
+    const uint8_t* canvas = (cur == 0 ? a0 : (cur == 1 ? a1 : a2)) + d.off + (long long)kPadY * d.pitch + kPadX;
+    const uintptr_t ad = reinterpret_cast<uintptr_t>(d.user);
+    const int m = (int)(ad & 3u);
+    uint32_t* dw = reinterpret_cast<uint32_t*>(ad - (uintptr_t)m);
+    const long long nbytes = (long long)d.rows * d.cols;
+    const long long total = (m + nbytes + 3) / 4;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < total;
+         w += (long long)gridDim.x * blockDim.x) {
+        const long long l0 = 4 * w - m;  // image byte index of the word's first byte
+        long long first = l0 < 0 ? 0 : l0;
+        long long r = first / d.cols;
+        int col = (int)(first - r * d.cols);
+        uint32_t v = 0;
+        int nb = 0;
+        for (int b = (int)(first - l0); b < 4 && l0 + b < nbytes; ++b) {
+            v |= (uint32_t)canvas[r * d.pitch + col] << (8 * b);
+            ++nb;
+            if (++col == d.cols) {
+                col = 0;
+                ++r;
+            }
+        }
+        if (nb == 4) {
+            dw[w] = v;
+        } else {
+            uint8_t* db = reinterpret_cast<uint8_t*>(dw + w);
+            for (int b = 0; b < 4; ++b)
+                if (l0 + b >= 0 && l0 + b < nbytes) db[b] = (uint8_t)(v >> (8 * b));
+        }
+    }
+}
+
+// tile_img[b] = the image that fused tile b belongs to.
+__global__ void tile_map_kernel(const ImgDesc* __restrict__ imgs, int nimg, int total_tiles, int* __restrict__ tile_img) {
+    const int i = blockIdx.x;
+    const int t0 = imgs[i].tile0;
+    const int t1 = i + 1 < nimg ? imgs[i + 1].tile0 : total_tiles;
+    for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) tile_img[t] = i;
+}
+
+static unsigned batch_copy_ctas(long long max_words, int nimg, int sms) {
+    long long g = (max_words + 2047) / 2048;
+    const long long cap = nimg > 0 ? ((long long)sms * 16 + nimg - 1) / nimg : 1;
+    const long long lim = cap > 16 ? cap : 16;
+    if (g > lim) g = lim;
+    if (g < 1) g = 1;
+    return (unsigned)g;
+}
+
+cudaError_t launch_copy_in_batch(const ImgDesc* imgs, int nimg, long long max_words, uint8_t* arena, int sms,
+                                 cudaStream_t s) {
+    if (nimg <= 0) return cudaSuccess;
+    copy_in_batch_kernel<<<dim3(batch_copy_ctas(max_words, nimg, sms), (unsigned)nimg), 256, 0, s>>>(imgs, arena);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_copy_out_batch(const Ctrl* c, uint8_t* const arena[3], const ImgDesc* imgs, int nimg,
+                                  long long max_words, int sms, cudaStream_t s) {
+    if (nimg <= 0) return cudaSuccess;
+    copy_out_batch_kernel<<<dim3(batch_copy_ctas(max_words, nimg, sms), (unsigned)nimg), 256, 0, s>>>(
+        c, arena[0], arena[1], arena[2], imgs);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tile_map(const ImgDesc* imgs, int nimg, int total_tiles, int* tile_img, cudaStream_t s) {
+    if (nimg <= 0) return cudaSuccess;
+    tile_map_kernel<<<(unsigned)nimg, 256, 0, s>>>(imgs, nimg, total_tiles, tile_img);
+    return cudaGetLastError();
+}
+
 }  // namespace hg

@@ -1,15 +1,16 @@
 // Host runtime behind the C ABI declared in include/hgrms.h.
 //
-// One call of hgrms_denoise:
-//   1. copy the image into canvas A (padded, 16-byte aligned rows),
+// One call of hgrms_denoise (or one chunk of hgrms_denoise_batch, whose
+// images are laid out side by side in the same buffers):
+//   1. copy the image(s) into canvas A (padded, 16-byte aligned rows),
 //   2. reset the device control block (k = 0, current canvas = A),
 //   3. enqueue the passes (Section 2's iteration): by default one fused
-//      launch of T passes on shared-memory tiles (the passes where many
-//      pixels change), then one list-pass launch per remaining pass, which
-//      evaluates only the windows around the pixels the previous pass
-//      changed.  The last CTA of each launch updates k, the converged flag
-//      and the current canvas on the device, so no launch waits for the
-//      host; launches after the end return at once,
+//      launch of T passes on shared-memory tiles of every image (the passes
+//      where many pixels change), then one persistent launch that runs each
+//      remaining pass as a list pass, evaluating only the windows around the
+//      pixels the previous pass changed.  k, the converged flag and the
+//      current canvas are kept on the device, so no launch waits for the
+//      host,
 //   4. copy the current canvas back and read k with one device-to-host copy.
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -49,6 +50,20 @@ struct hgrms_ctx {
     std::vector<cudaEvent_t> events;
     std::vector<float> launch_ms;  // per-launch durations of the last call (HGRMS_OPT_TIMING)
     std::vector<int> launch_kind;  // 0 = fused, 1 = list pass, 2 = unfused
+    // Image table of the hybrid schedule (device copy, pinned staging copy),
+    // the fused tile -> image map and the per-image k of a batch.
+    hg::ImgDesc* d_desc = nullptr;
+    size_t desc_cap = 0;
+    hg::ImgDesc* host_desc = nullptr;
+    size_t host_desc_cap = 0;
+    int* tile_img = nullptr;
+    size_t tile_cap = 0;
+    unsigned* img_k = nullptr;
+    unsigned* host_img_k = nullptr;
+    size_t img_k_cap = 0;
+    std::vector<hg::ImgDesc> table_cache;  // what d_desc and tile_img hold now
+    int table_tiles = -1;
+    int opt_batch_mb = 0;
 };
 
 namespace hg {
@@ -142,8 +157,11 @@ struct Plan {
     int bm_words;
 };
 
+// Launch plan of the unfused and fused-only schedules (the hybrid schedule
+// is run_hybrid's).
 int make_plan(hgrms_ctx* h, int rows, int cols, int beta, int max_k, Plan* p) {
     p->schedule = h->opt_kernel;
+    if (p->schedule == kHybrid) return HGRMS_EINVAL;
     p->fused = p->schedule != kPlain;
     p->fe = nullptr;
     p->list_cap = 0;
@@ -157,17 +175,8 @@ int make_plan(hgrms_ctx* h, int rows, int cols, int beta, int max_k, Plan* p) {
         const long long need_w = hg::kPadX + (long long)p->tiles_x * p->fe->TW + 16;
         p->pitch = (need_w + 127) / 128 * 128;
         p->crows = hg::kPadY + (long long)p->tiles_y * p->fe->TH + 16;
-        if (p->schedule == kHybrid) {
-            p->fused_launches = max_k > 0 ? 1 : 0;
-            p->launches = max_k > p->T ? 2 : p->fused_launches;  // + one launch running every list pass
-            p->map_words = 0;
-            p->list_cap = h->opt_list_cap > 0 ? (size_t)h->opt_list_cap
-                                              : (size_t)rows * (size_t)cols / 4 + 65536;
-            p->bm_words = (cols + 31) / 32 + 1;
-        } else {
-            p->fused_launches = p->launches = (max_k + p->T - 1) / p->T;
-            p->map_words = (p->tiles_x * p->fe->TW + 31) / 32 + 2;
-        }
+        p->fused_launches = p->launches = (max_k + p->T - 1) / p->T;
+        p->map_words = (p->tiles_x * p->fe->TW + 31) / 32 + 2;
     } else {
         p->T = 1;
         p->tiles_x = p->tiles_y = 0;
@@ -233,8 +242,242 @@ int ensure_events(hgrms_ctx* h, size_t n) {
     return HGRMS_OK;
 }
 
-// Everything of one denoise except argument checks.  `dev` tells whether img
-// is device memory.
+// Device and pinned host buffers of the image table for n images and
+// `tiles` fused tiles; a reallocation invalidates the cached table.
+int ensure_table(hgrms_ctx* h, size_t n, size_t tiles, bool per_image_k) {
+    if (n > h->desc_cap) {
+        if (h->d_desc) cudaFree(h->d_desc);
+        if (h->host_desc) cudaFreeHost(h->host_desc);
+        h->d_desc = nullptr;
+        h->host_desc = nullptr;
+        h->desc_cap = 0;
+        h->table_tiles = -1;
+        HG_TRY(h, cudaMalloc(&h->d_desc, n * sizeof(hg::ImgDesc)));
+        HG_TRY(h, cudaMallocHost(&h->host_desc, n * sizeof(hg::ImgDesc)));
+        h->desc_cap = n;
+    }
+    if (tiles > h->tile_cap) {
+        if (h->tile_img) cudaFree(h->tile_img);
+        h->tile_img = nullptr;
+        h->tile_cap = 0;
+        h->table_tiles = -1;
+        HG_TRY(h, cudaMalloc(&h->tile_img, tiles * sizeof(int)));
+        h->tile_cap = tiles;
+    }
+    if (per_image_k && n > h->img_k_cap) {
+        if (h->img_k) cudaFree(h->img_k);
+        if (h->host_img_k) cudaFreeHost(h->host_img_k);
+        h->img_k = nullptr;
+        h->host_img_k = nullptr;
+        h->img_k_cap = 0;
+        HG_TRY(h, cudaMalloc(&h->img_k, n * sizeof(unsigned)));
+        HG_TRY(h, cudaMallocHost(&h->host_img_k, n * sizeof(unsigned)));
+        h->img_k_cap = n;
+    }
+    return HGRMS_OK;
+}
+
+// Bits needed for values 0 .. v (at least 1).
+int bits_for(long long v) {
+    int b = 1;
+    while (b < 62 && (1ll << b) <= v) ++b;
+    return b;
+}
+
+struct BatchImg {
+    uint8_t* ptr;
+    int rows, cols;
+    bool dev;  // device memory of the handle's device (else host memory)
+};
+
+// Canvas, bitmap and list bytes the hybrid schedule needs for one image (a
+// chunk needs the sum, plus a small constant).
+long long hybrid_bytes(const hg::FusedEntry* fe, int rows, int cols) {
+    const long long tiles_x = (cols + fe->TW - 1) / fe->TW, tiles_y = (rows + fe->TH - 1) / fe->TH;
+    const long long pitch = (hg::kPadX + tiles_x * fe->TW + 16 + 127) / 128 * 128;
+    const long long crows = hg::kPadY + tiles_y * fe->TH + 16;
+    const long long px = (long long)rows * cols;
+    return 3 * pitch * crows + 4 * 4 * (long long)rows * ((cols + 31) / 32 + 1) + 4 * 4 * (px / 4) + 4 * tiles_x * tiles_y;
+}
+
+// The hybrid schedule (one fused launch of T passes over the tiles of every
+// image, then one persistent launch running the remaining passes as list
+// passes) for n images at once.  k_out[i] gets image i's k; the return value
+// is HGRMS_OK or a negative code.  Every image runs the same sequence of
+// passes; the sequence ends when a pass changes no pixel of any image or
+// after max_k passes, and image i's k is the number of the last pass that
+// changed one of its pixels (an image that a pass leaves unchanged is at a
+// fixed point, so later passes leave it unchanged too).
+int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int max_k, int* k_out) {
+    const int T = h->opt_passes > 0 ? h->opt_passes : default_passes(beta);
+    const hg::FusedEntry* fe = find_fused(beta, T);
+    if (!fe) return HGRMS_EINVAL;
+    const bool per_image_k = n > 1;
+    // Layout: image i's canvas at offset off_i of each arena, its bitmap at
+    // word bm_off_i of each bitmap arena, its tiles from tile0_i.
+    long long canvas_total = 0, bm_total = 0, tiles_total = 0, px_total = 0, max_words = 0;
+    int max_rows = 1, max_cols = 1;
+    int rc = ensure_table(h, (size_t)n, 0, false);
+    if (rc < 0) return rc;
+    for (int i = 0; i < n; ++i) {
+        const int rows = im[i].rows, cols = im[i].cols;
+        const int tiles_x = (cols + fe->TW - 1) / fe->TW, tiles_y = (rows + fe->TH - 1) / fe->TH;
+        const long long pitch = (hg::kPadX + (long long)tiles_x * fe->TW + 16 + 127) / 128 * 128;
+        const long long crows = hg::kPadY + (long long)tiles_y * fe->TH + 16;
+        hg::ImgDesc d;
+        memset(&d, 0, sizeof(d));
+        d.off = canvas_total;
+        d.bm_off = bm_total;
+        d.pitch = (int)pitch;
+        d.rows = rows;
+        d.cols = cols;
+        d.tiles_x = tiles_x;
+        d.tile0 = (int)tiles_total;
+        d.bm_words = (cols + 31) / 32 + 1;
+        d.user = (n > 1 && im[i].dev) ? im[i].ptr : nullptr;
+        h->host_desc[i] = d;
+        canvas_total += pitch * crows;
+        bm_total += (long long)rows * d.bm_words;
+        tiles_total += (long long)tiles_x * tiles_y;
+        px_total += (long long)rows * cols;
+        const long long words = ((long long)rows * cols + 3) / 4 + 1;
+        if (words > max_words) max_words = words;
+        if (rows > max_rows) max_rows = rows;
+        if (cols > max_cols) max_cols = cols;
+    }
+    if (tiles_total > 0x7fffffffll) return HGRMS_EINVAL;
+    // Entry packing: a single image uses 16 + 16 bits (the list loop's
+    // single-image form assumes it), a batch the fewest bits its sizes need.
+    const int xb = n > 1 ? bits_for(max_cols - 1) : 16, yb = n > 1 ? bits_for(max_rows - 1) : 16;
+    if (xb + yb + (n > 1 ? bits_for(n - 1) : 0) > 32) return HGRMS_EINVAL;  // chunking keeps this from happening
+    const size_t list_cap = h->opt_list_cap > 0 ? (size_t)h->opt_list_cap : (size_t)(px_total / 4 + 65536);
+    rc = ensure_canvas(h, (size_t)canvas_total);
+    if (rc < 0) return rc;
+    rc = ensure_lists(h, list_cap, (size_t)bm_total);
+    if (rc < 0) return rc;
+    rc = ensure_table(h, (size_t)n, (size_t)tiles_total, per_image_k);
+    if (rc < 0) return rc;
+    cudaStream_t s = h->stream;
+    // The table and tile map on the device (skipped when unchanged).
+    const bool same = h->table_tiles == (int)tiles_total && h->table_cache.size() == (size_t)n &&
+                      memcmp(h->table_cache.data(), h->host_desc, (size_t)n * sizeof(hg::ImgDesc)) == 0;
+    if (!same) {
+        HG_TRY(h, cudaMemcpyAsync(h->d_desc, h->host_desc, (size_t)n * sizeof(hg::ImgDesc), cudaMemcpyHostToDevice, s));
+        HG_TRY(h, hg::launch_tile_map(h->d_desc, n, (int)tiles_total, h->tile_img, s));
+        h->table_cache.assign(h->host_desc, h->host_desc + n);
+        h->table_tiles = (int)tiles_total;
+    }
+    // Images in: device images by kernel, host images by 2-D copies.
+    if (n == 1 && im[0].dev) {
+        HG_TRY(h, hg::launch_copy_in(im[0].ptr, im[0].rows, im[0].cols, h->canvas[0], h->host_desc[0].pitch, h->sms, s));
+    } else {
+        HG_TRY(h, hg::launch_copy_in_batch(h->d_desc, n, max_words, h->canvas[0], h->sms, s));
+        for (int i = 0; i < n; ++i) {
+            if (im[i].dev) continue;
+            const hg::ImgDesc& d = h->host_desc[i];
+            HG_TRY(h, cudaMemcpy2DAsync(h->canvas[0] + d.off + (long long)hg::kPadY * d.pitch + hg::kPadX, (size_t)d.pitch,
+                                        im[i].ptr, (size_t)d.cols, (size_t)d.cols, (size_t)d.rows,
+                                        cudaMemcpyHostToDevice, s));
+        }
+    }
+    HG_TRY(h, hg::launch_ctrl_init(h->ctrl, (unsigned)max_k, s));
+    HG_TRY(h, cudaMemsetAsync(h->bitmaps, 0, 4 * (size_t)bm_total * sizeof(uint32_t), s));
+    HG_TRY(h, cudaMemsetAsync(h->bar, 0, sizeof(hg::GridBar), s));
+    if (per_image_k) HG_TRY(h, cudaMemsetAsync(h->img_k, 0, (size_t)n * sizeof(unsigned), s));
+    hg::PassArgs a;
+    memset(&a, 0, sizeof(a));
+    for (int i = 0; i < 3; ++i) a.canvas[i] = h->canvas[i];
+    a.pitch = h->host_desc[0].pitch;
+    a.rows = h->host_desc[0].rows;
+    a.cols = h->host_desc[0].cols;
+    a.alpha = alpha;
+    a.tiles_x = h->host_desc[0].tiles_x;
+    a.ctrl = h->ctrl;
+    a.chg_maps = nullptr;
+    a.map_words = 0;
+    for (int i = 0; i < 4; ++i) {
+        a.lists[i] = h->lists + i * list_cap;
+        a.bitmaps[i] = h->bitmaps + i * (size_t)bm_total;
+    }
+    a.list_cap = (unsigned)list_cap;
+    a.bm_words = h->host_desc[0].bm_words;
+    a.write_prev = 1;
+    a.bar = h->bar;
+    a.imgs = h->d_desc;
+    a.nimg = n;
+    a.xb = xb;
+    a.yb = yb;
+    a.tile_img = h->tile_img;
+    a.bm_total = bm_total;
+    a.img_k = per_image_k ? h->img_k : nullptr;
+    const int launches = max_k > 0 ? (max_k > T ? 2 : 1) : 0;
+    const bool timed = h->opt_timing != 0;
+    if (timed) {
+        rc = ensure_events(h, 4);
+        if (rc < 0) return rc;
+    }
+    for (int i = 0; i < launches; ++i) {
+        if (timed) HG_TRY(h, cudaEventRecord(h->events[2 * i], s));
+        if (i == 0)
+            HG_TRY(h, fe->launch(a, (int)tiles_total, s));
+        else
+            HG_TRY(h, hg::launch_list(beta, a, h->sms, s));
+        if (timed) HG_TRY(h, cudaEventRecord(h->events[2 * i + 1], s));
+    }
+    if (n == 1 && im[0].dev) {
+        HG_TRY(h, hg::launch_copy_out(h->ctrl, h->canvas, h->host_desc[0].pitch, im[0].ptr, im[0].rows, im[0].cols,
+                                      h->sms, s));
+    } else {
+        HG_TRY(h, hg::launch_copy_out_batch(h->ctrl, h->canvas, h->d_desc, n, max_words, h->sms, s));
+    }
+    HG_TRY(h, cudaMemcpyAsync(h->host_ctrl, h->ctrl, sizeof(hg::Ctrl), cudaMemcpyDeviceToHost, s));
+    if (per_image_k)
+        HG_TRY(h, cudaMemcpyAsync(h->host_img_k, h->img_k, (size_t)n * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    HG_TRY(h, cudaStreamSynchronize(s));
+    const hg::Ctrl c = *h->host_ctrl;
+    bool host_out = false;
+    for (int i = 0; i < n; ++i) {
+        if (im[i].dev) continue;
+        const hg::ImgDesc& d = h->host_desc[i];
+        HG_TRY(h, cudaMemcpy2DAsync(im[i].ptr, (size_t)d.cols,
+                                    h->canvas[c.cur] + d.off + (long long)hg::kPadY * d.pitch + hg::kPadX,
+                                    (size_t)d.pitch, (size_t)d.cols, (size_t)d.rows, cudaMemcpyDeviceToHost, s));
+        host_out = true;
+    }
+    if (host_out) HG_TRY(h, cudaStreamSynchronize(s));
+    if (timed) {
+        for (int i = 0; i < launches; ++i) {
+            float ms = 0.f;
+            HG_TRY(h, cudaEventElapsedTime(&ms, h->events[2 * i], h->events[2 * i + 1]));
+            h->launch_ms.push_back(ms);
+            h->launch_kind.push_back(i == 0 ? 0 : 1);
+            if (i < (int)c.work_launches)
+                h->stats.kernel_ms += ms;
+            else
+                h->stats.idle_kernel_ms += ms;
+        }
+    }
+    if (c.error) {
+        h->last_cuda_error = 0;
+        return HGRMS_ETIMEOUT;
+    }
+    for (int i = 0; i < n; ++i) k_out[i] = per_image_k ? (int)h->host_img_k[i] : (int)c.k;
+    h->stats.launches += launches;
+    h->stats.passes_per_launch = T;
+    h->stats.tile_rows = fe->TH;
+    h->stats.tile_cols = fe->TW;
+    h->stats.ctas_per_launch += tiles_total;
+    h->stats.passes_executed += (int)c.executed;
+    h->stats.evals_fused += (long long)c.evals_fused;
+    h->stats.evals_list += (long long)c.evals_list;
+    h->stats.work_launches += (int)c.work_launches;
+    h->stats.passes += (int)(c.k + c.converged);
+    h->converged = (int)c.converged;
+    return HGRMS_OK;
+}
+
+// One denoise with the unfused or fused-only schedule, except argument
+// checks.  `dev` tells whether img is device memory.
 int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int beta, int max_k,
                 bool dev, bool sync_and_finish) {
     Plan p;
@@ -285,7 +528,13 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     a.list_cap = (unsigned)p.list_cap;
     a.bm_words = p.bm_words;
     a.bar = h->bar;
-    a.write_prev = p.schedule == kHybrid ? 1 : 0;
+    a.write_prev = 0;
+    a.imgs = nullptr;
+    a.nimg = 1;
+    a.xb = a.yb = 16;
+    a.tile_img = nullptr;
+    a.bm_total = 0;
+    a.img_k = nullptr;
     // Per-launch timing is limited to calls of at most kMaxTimedLaunches launches.
     constexpr int kMaxTimedLaunches = 4096;
     const bool timed = h->opt_timing && p.launches <= kMaxTimedLaunches;
@@ -296,7 +545,7 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     for (int i = 0; i < p.launches; ++i) {
         if (timed) HG_TRY(h, cudaEventRecord(h->events[2 * i], s));
         if (i < p.fused_launches)
-            HG_TRY(h, p.fe->launch(a, p.tiles_y, s));
+            HG_TRY(h, p.fe->launch(a, p.tiles_x * p.tiles_y, s));
         else if (p.fused)
             HG_TRY(h, hg::launch_list(beta, a, h->sms, s));
         else
@@ -391,6 +640,11 @@ HG_EXPORT void hgrms_destroy(hgrms_t h) {
         if (h->lists) cudaFree(h->lists);
         if (h->bitmaps) cudaFree(h->bitmaps);
         if (h->host_ctrl) cudaFreeHost(h->host_ctrl);
+        if (h->d_desc) cudaFree(h->d_desc);
+        if (h->host_desc) cudaFreeHost(h->host_desc);
+        if (h->tile_img) cudaFree(h->tile_img);
+        if (h->img_k) cudaFree(h->img_k);
+        if (h->host_img_k) cudaFreeHost(h->host_img_k);
         for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     }
     delete h;
@@ -406,7 +660,11 @@ HG_EXPORT int hgrms_denoise(hgrms_t h, uint8_t* img, int rows, int cols, int alp
     h->stats = hgrms_stats_t{};
     h->launch_ms.clear();
     h->launch_kind.clear();
-    return denoise_one(h, img, rows, cols, alpha, beta, max_k, kind == 1, true);
+    if (h->opt_kernel != kHybrid) return denoise_one(h, img, rows, cols, alpha, beta, max_k, kind == 1, true);
+    const BatchImg bi{img, rows, cols, kind == 1};
+    int k = 0;
+    rc = run_hybrid(h, &bi, 1, alpha, beta, max_k, &k);
+    return rc < 0 ? rc : k;
 }
 
 HG_EXPORT int hgrms_denoise_batch(hgrms_t h, uint8_t* const* imgs, const int* rows, const int* cols, int n,
@@ -423,10 +681,45 @@ HG_EXPORT int hgrms_denoise_batch(hgrms_t h, uint8_t* const* imgs, const int* ro
         if (kind0 == -2) kind0 = kind;
         if (kind != kind0) return HGRMS_EINVAL;
     }
-    hgrms_stats_t acc{};
-    int all_conv = 1;
     h->launch_ms.clear();
     h->launch_kind.clear();
+    if (h->opt_kernel == kHybrid && n > 0) {
+        // Chunks of consecutive images, each run as one batched schedule: a
+        // chunk ends before the image that would exceed the memory budget,
+        // the image count of one launch or the 32-bit change-list packing.
+        const int T = h->opt_passes > 0 ? h->opt_passes : default_passes(beta);
+        const hg::FusedEntry* fe = find_fused(beta, T);
+        if (!fe) return HGRMS_EINVAL;
+        const long long budget = (long long)(h->opt_batch_mb > 0 ? h->opt_batch_mb : 8192) << 20;
+        std::vector<BatchImg> bi((size_t)n);
+        for (int i = 0; i < n; ++i) bi[i] = BatchImg{imgs[i], rows[i], cols[i], kind0 == 1};
+        h->stats = hgrms_stats_t{};
+        int all_conv = 1;
+        for (int start = 0; start < n;) {
+            int end = start, mr = 1, mc = 1;
+            long long bytes = 0;
+            while (end < n) {
+                const long long nb = hybrid_bytes(fe, rows[end], cols[end]);
+                const int mr2 = rows[end] > mr ? rows[end] : mr, mc2 = cols[end] > mc ? cols[end] : mc;
+                const int cnt = end - start + 1;
+                const bool fits = cnt <= hg::kMaxBatchImages && bytes + nb <= budget &&
+                                  bits_for(mc2 - 1) + bits_for(mr2 - 1) + (cnt > 1 ? bits_for(cnt - 1) : 0) <= 32;
+                if (!fits && end > start) break;
+                bytes += nb;
+                mr = mr2;
+                mc = mc2;
+                ++end;
+            }
+            const int rc = run_hybrid(h, bi.data() + start, end - start, alpha, beta, max_k, k_out + start);
+            if (rc < 0) return rc;
+            start = end;
+        }
+        for (int i = 0; i < n; ++i) all_conv &= k_out[i] < max_k ? 1 : 0;
+        h->converged = all_conv;
+        return HGRMS_OK;
+    }
+    hgrms_stats_t acc{};
+    int all_conv = 1;
     for (int i = 0; i < n; ++i) {
         h->stats = hgrms_stats_t{};
         const int k = denoise_one(h, imgs[i], rows[i], cols[i], alpha, beta, max_k, kind0 == 1, true);
@@ -492,6 +785,10 @@ HG_EXPORT int hgrms_set_option(hgrms_t h, int option, int value) {
         case HGRMS_OPT_LIST_CAP:
             if (value < 0) return HGRMS_EINVAL;
             h->opt_list_cap = value;
+            return HGRMS_OK;
+        case HGRMS_OPT_BATCH_MB:
+            if (value < 0) return HGRMS_EINVAL;
+            h->opt_batch_mb = value;
             return HGRMS_OK;
         default: return HGRMS_EINVAL;
     }

@@ -30,6 +30,7 @@ HGRMS_OPT_KERNEL = 1
 HGRMS_OPT_PASSES = 2
 HGRMS_OPT_TIMING = 3
 HGRMS_OPT_LIST_CAP = 4
+HGRMS_OPT_BATCH_MB = 5
 
 # Every symbol the header declares (the CPU tests check the library exports them).
 EXPORTED = (

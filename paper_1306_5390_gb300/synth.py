@@ -188,3 +188,27 @@ def workload_8192(beta: int = 1, size: int = 8192):
     clean, noisy = noisy_image(size, size, 0.30, seed)
     return dict(name=f"{size}x{size} sp30 a10 b{beta}", clean=clean,
                 noisy=noisy, alpha=10, beta=beta, max_k=32, seed=seed)
+
+
+def batch_shapes(n_images: int = 512, min_side: int = 128, max_side: int = 2048, seed: int = None):
+    """Side lengths of the uneven batch: each side uniform in
+    [min_side, max_side] (independently, so the aspect ratio is random)."""
+    rng = np.random.Generator(np.random.PCG64(seed_for(3, 0) if seed is None else seed))
+    return [(int(r), int(c)) for r, c in rng.integers(min_side, max_side + 1, size=(n_images, 2))]
+
+
+def workload_batch(n_images: int = 512, min_side: int = 128, max_side: int = 2048, first: int = 0,
+                   last: int = None):
+    """The uneven batch: images with sides uniform in 128..2048, impulse
+    density uniform in 5..70 %, alpha 10, beta 1, max_k 32.  Yields one dict
+    per image (images first .. last - 1, default all; each is generated from
+    its own seed, so a slice is the same images as in the whole batch)."""
+    shapes = batch_shapes(n_images, min_side, max_side)
+    for i in range(first, n_images if last is None else min(last, n_images)):
+        rows, cols = shapes[i]
+        seed = seed_for(3, 1 + i)
+        rng = np.random.Generator(np.random.PCG64(seed))
+        density = float(rng.uniform(0.05, 0.70))
+        clean, noisy = noisy_image(rows, cols, density, seed)
+        yield dict(name=f"{rows}x{cols} sp{density * 100:.1f} a10 b1", clean=clean, noisy=noisy,
+                   alpha=10, beta=1, max_k=32, seed=seed, density=density, image=i)
