@@ -191,9 +191,10 @@ def run_ours(args, rank, world, local):
                 pb[key] += st[key]
             for key in ("work_launches", "launches", "passes_executed", "evals_fused", "evals_list"):
                 pb[key] += st[key]
-            for ms, kind in d.launch_times()[: st["work_launches"]]:
-                pb["ms_by_kind"][kind] += ms
-                pb["n_by_kind"][kind] += 1
+            for ms, kind in d.launch_times():
+                if kind < 3:  # 3: a launch that ran no pass
+                    pb["ms_by_kind"][kind] += ms
+                    pb["n_by_kind"][kind] += 1
             pb["T"] = st["passes_per_launch"]
             pb["ctas"] = st["ctas_per_launch"]
             pb["calls"] += 1

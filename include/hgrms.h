@@ -135,9 +135,10 @@ int hgrms_denoise_noalloc(uint8_t* img, int rows, int cols, int alpha, int beta,
 /* ---- Tuning and measurement (not part of the method) ------------------ */
 
 /* Options for hgrms_set_option. */
-#define HGRMS_OPT_KERNEL   1 /* 0 = one fused multi-pass tile launch, then one persistent launch that
-                                 runs every remaining pass as a list pass (default); 1 = unfused
-                                 one-pass kernel for every pass; 2 = fused tile launches only */
+#define HGRMS_OPT_KERNEL   1 /* 0 = fused multi-pass tile launches while many pixels change, then one
+                                 persistent launch that runs every remaining pass as a list pass
+                                 (default); 1 = unfused one-pass kernel for every pass; 2 = fused tile
+                                 launches only */
 #define HGRMS_OPT_PASSES   2 /* passes fused per launch; 0 = the built-in choice for beta */
 #define HGRMS_OPT_TIMING   3 /* 1 = time every denoising launch with CUDA events (see hgrms_stats) */
 #define HGRMS_OPT_LIST_CAP 4 /* capacity of the change lists of list passes (0 = rows*cols/4 + 65536);
@@ -145,6 +146,11 @@ int hgrms_denoise_noalloc(uint8_t* img, int rows, int cols, int alpha, int beta,
 #define HGRMS_OPT_BATCH_MB 5 /* hgrms_denoise_batch: device memory (MiB) one batched launch may use for
                                 canvases, change lists and bitmaps (0 = 8192); larger batches run as
                                 several chunks of consecutive images, with identical results */
+#define HGRMS_OPT_RELAUNCH_PPM 6 /* default schedule: after a fused launch, another fused launch runs
+                                    (instead of list passes) while a list pass would evaluate more than
+                                    this many pixels per million pixels of the call, up to 8 times
+                                    (0 = built-in: 25000 for beta 1, up to 3 times, never for
+                                    beta >= 2; 1000000 or more = never) */
 
 /* Set an option.  Returns HGRMS_OK or HGRMS_EINVAL (unknown option or value,
  * e.g. a pass count that has no compiled kernel for some beta is rejected at
@@ -176,8 +182,10 @@ int hgrms_stats(hgrms_t h, hgrms_stats_t* out);
 
 /* Per-launch durations (ms) of the last call, recorded when HGRMS_OPT_TIMING
  * is on, in launch order; kind[i] (if kind is not NULL) is 0 for a fused tile
- * launch, 1 for the launch running the list passes, 2 for an unfused pass.  Copies at most n entries
- * and returns the number recorded, or HGRMS_EINVAL. */
+ * launch, 1 for the launch running the list passes, 2 for an unfused pass and
+ * 3 for a launch that ran no pass (the call had finished, or the schedule
+ * skipped it).  Copies at most n entries and returns the number recorded, or
+ * HGRMS_EINVAL. */
 int hgrms_launch_times(hgrms_t h, float* ms, int* kind, int n);
 
 /* The passes per launch the built-in choice uses for beta (1..7), or

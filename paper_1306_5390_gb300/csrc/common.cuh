@@ -37,6 +37,9 @@ struct Ctrl {
     unsigned executed;   // passes executed by launches that did work
     unsigned list_n[4];  // entries appended to change list 0..3 (> capacity: overflow)
     unsigned error;      // 1: a bounded device wait gave up
+    unsigned fused_work; // fused launches that ran passes
+    unsigned dense;      // hybrid schedule: 1 = the next fused launch runs (many pixels changed)
+    unsigned tile_next[2];  // tile queue of fused launch L: counter L & 1
     // Pixel evaluations the passes needed (core pixels only: a dense pass
     // counts every image pixel, a list pass the pixels it claimed), by kernel.
     unsigned long long evals_fused;
@@ -135,6 +138,15 @@ struct PassArgs {
     const int* tile_img;
     long long bm_total;       // words in one bitmap arena
     unsigned* img_k;
+    int ntiles;               // fused-kernel tiles (all images)
+    // Hybrid schedule: fused launch L (L = fused launches that ran before
+    // it) writes change set L % 4, reads set (L + 3) % 4 and clears set
+    // (L + 2) % 4.  Launches after the first run only while the previous
+    // one's last pass changed so many pixels that a list pass would evaluate
+    // more than relaunch_evals pixels; the list-pass loop then starts from
+    // the last fused launch's set.
+    int hybrid;
+    long long relaunch_evals;
 };
 
 // Passes the launch must run: 0 when the call has finished.
@@ -154,7 +166,8 @@ __device__ __forceinline__ int launch_passes(const Ctrl* c, int T) {
 // the image is a fixed point (every later pass is a no-op, so the canvas
 // written by this launch holds the final image).  new_cur / new_aux are the
 // canvases the launch leaves as `cur` and `aux`.
-__device__ __forceinline__ void finish_launch(Ctrl* c, unsigned cta_mask, int np, unsigned nctas,
+// Returns true in the last CTA.
+__device__ __forceinline__ bool finish_launch(Ctrl* c, unsigned cta_mask, int np, unsigned nctas,
                                               unsigned new_cur, unsigned new_aux) {
     if (cta_mask) atomicOr(&c->mask, cta_mask);
     __threadfence();
@@ -172,7 +185,9 @@ __device__ __forceinline__ void finish_launch(Ctrl* c, unsigned cta_mask, int np
         c->executed += (unsigned)np;
         c->done = 0u;
         __threadfence();
+        return true;
     }
+    return false;
 }
 
 // Appends to a global change list staged per warp in shared memory, so that

@@ -400,268 +400,333 @@ __device__ __forceinline__ void list_pass(PassCtx<B, T>& c, const uint16_t* prev
     }
 }
 
+// Persistent: each CTA takes tiles from a queue (one counter per launch in
+// the control block) until none are left, so a launch whose work is done, or
+// that the hybrid schedule skips, costs one short wave.
 template <int B, int T>
 __global__ void __launch_bounds__(FusedGeo<B, T>::kThreads, 2)
 fused_kernel(PassArgs a) {
     using G = FusedGeo<B, T>;
     extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ int s_np;
-    __shared__ unsigned s_cur, s_aux, s_launch, s_k, s_img;
+    __shared__ int s_np, s_tile;
+    __shared__ unsigned s_cur, s_aux, s_launch, s_k, s_img, s_nclr, s_nin;
     __shared__ ImgDesc s_d;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
+    Ctrl* ctrl = a.ctrl;
     if (tid == 0) {
-        s_np = launch_passes(a.ctrl, T);
-        s_cur = __ldcg(&a.ctrl->cur);
-        s_aux = __ldcg(&a.ctrl->aux);
-        s_launch = __ldcg(&a.ctrl->work_launches);
-        s_k = __ldcg(&a.ctrl->k);
-        // This tile's image: from the image table, else the single image
-        // described by the arguments.
-        ImgDesc d;
-        unsigned img = 0;
-        if (a.imgs) {
-            img = (unsigned)__ldg(a.tile_img + blockIdx.x);
-            d = load_desc(a.imgs, img);
-        } else {
-            d.off = 0;
-            d.bm_off = 0;
-            d.pitch = (int)a.pitch;
-            d.rows = a.rows;
-            d.cols = a.cols;
-            d.tiles_x = a.tiles_x;
-            d.tile0 = 0;
-            d.bm_words = a.bm_words;
-            d.user = nullptr;
-        }
-        s_d = d;
-        s_img = img;
+        int np = launch_passes(ctrl, T);
+        // Every launch that did work before this one was a fused launch.
+        const unsigned L = __ldcg(&ctrl->work_launches);
+        if (a.hybrid && L > 0 && __ldcg(&ctrl->dense) == 0u) np = 0;  // few changes left: the list passes take over
+        s_np = np;
+        s_cur = __ldcg(&ctrl->cur);
+        s_aux = __ldcg(&ctrl->aux);
+        s_launch = L;
+        s_k = __ldcg(&ctrl->k);
+        s_nclr = a.hybrid ? __ldcg(&ctrl->list_n[(L + 2) & 3]) : 0u;
+        s_nin = a.hybrid ? __ldcg(&ctrl->list_n[(L + 3) & 3]) : 0u;
     }
     __syncthreads();
     const int np = s_np;
     if (np == 0) return;
     const unsigned L = s_launch;
     const unsigned cur = s_cur, aux = s_aux, third = 3u - s_cur - s_aux;
-    const unsigned img = s_img;
-    const long long pitch = s_d.pitch, coff = s_d.off, bm_off = s_d.bm_off;
-    const int rows = s_d.rows, cols = s_d.cols, bm_words = s_d.bm_words;
-    const uint8_t* src = a.canvas[cur] + coff;
-    uint8_t* dst = a.canvas[aux] + coff;
-    const int tile = (int)blockIdx.x - s_d.tile0;
-    const int tx = tile % s_d.tiles_x;
-    const int ty = tile / s_d.tiles_x;
-    const int x0 = tx * G::TW, y0 = ty * G::TH;
     uint32_t* buf0 = reinterpret_cast<uint32_t*>(smem);
     uint32_t* buf1 = reinterpret_cast<uint32_t*>(smem + G::kBufBytes);
     uint16_t* cand = reinterpret_cast<uint16_t*>(smem + G::kCandOff) + warp * G::kCandCap;
     uint16_t* lists = reinterpret_cast<uint16_t*>(smem + G::kListOff);  // 2 lists: pass t uses t & 1
     uint32_t* marks = reinterpret_cast<uint32_t*>(smem + G::kMarkOff);  // 2 bitmaps: pass t uses t & 1
     int* s_cnt = reinterpret_cast<int*>(smem + G::kCntOff);             // list counters, pass t uses t % 3
+    // Single-image pixel change maps (fused-only schedule).
     const bool use_maps = a.chg_maps != nullptr;
-    const size_t map_size = use_maps ? (size_t)rows * (size_t)a.map_words : 0;
+    const size_t map_size = use_maps ? (size_t)a.rows * (size_t)a.map_words : 0;
     uint32_t* map_out = use_maps ? a.chg_maps + (size_t)(L % 3u) * map_size : nullptr;
     const uint32_t* map_in = use_maps ? a.chg_maps + (size_t)((L + 2u) % 3u) * map_size : nullptr;
     uint32_t* map_clr = use_maps ? a.chg_maps + (size_t)((L + 1u) % 3u) * map_size : nullptr;
+    // Change sets of the hybrid schedule.
+    const int set_out = (int)(L & 3u), set_in = (int)((L + 3u) & 3u), set_clr = (int)((L + 2u) & 3u);
 
-    // Tile with halo: image rows [y0 - H, y0 + TH + H), columns [x0 - 16,
-    // x0 + TW + 16); always inside the canvas.  Bytes -> fp16 pairs, into
-    // both buffers (a list pass leaves unevaluated pixels as they are in its
-    // output buffer, so that buffer must start equal to the input).
+    // Launch-wide clearing, shared by all CTAs: the map the next launch
+    // writes, or the change set the next launch writes (its bitmap, by
+    // walking its list, or all of it after an overflow).
     {
-        const uint8_t* base = src + (long long)(kPadY + y0 - G::H) * pitch + x0;
-        constexpr int CH = G::SW / 16;
-        for (int i = tid; i < G::SH * CH; i += G::kThreads) {
-            const int r = i / CH, cc = i - r * CH;
-            const uint4 v = __ldg(reinterpret_cast<const uint4*>(base + (long long)r * pitch + cc * 16));
-            uint4 lo, hi;
-            lo.x = bytes_to_h2(v.x, 0x4140u); lo.y = bytes_to_h2(v.x, 0x4342u);
-            lo.z = bytes_to_h2(v.y, 0x4140u); lo.w = bytes_to_h2(v.y, 0x4342u);
-            hi.x = bytes_to_h2(v.z, 0x4140u); hi.y = bytes_to_h2(v.z, 0x4342u);
-            hi.z = bytes_to_h2(v.w, 0x4140u); hi.w = bytes_to_h2(v.w, 0x4342u);
-            uint4* d0 = reinterpret_cast<uint4*>(buf0 + r * G::SWW + cc * 8);
-            uint4* d1 = reinterpret_cast<uint4*>(buf1 + r * G::SWW + cc * 8);
-            d0[0] = lo;
-            d0[1] = hi;
-            d1[0] = lo;
-            d1[1] = hi;
-        }
-        for (int i = tid; i < 2 * G::kMarkWords; i += G::kThreads) marks[i] = 0u;
-        if (tid < 4) s_cnt[tid] = 0;
-        // Clear this CTA's share of the map the next launch writes.
-        for (size_t i = (size_t)blockIdx.x * G::kThreads + tid; i < map_size; i += (size_t)gridDim.x * G::kThreads)
-            map_clr[i] = 0u;  // map_size is 0 without maps
-    }
-    __syncthreads();
-    // Pass 0's "previous pass": the pixels the previous launch's last pass
-    // changed (global map), listed in list 1 / counter 2.
-    const bool from_map = use_maps && L > 0;
-    if (from_map) {
-        const int wlo = (x0 - kPadX) >> 5;  // floor division (x0 - 16 >= -16)
-        const int nw = ((x0 + G::TW + kPadX - 1) >> 5) - wlo + 1;
-        for (int i = tid; i < G::SH * nw; i += G::kThreads) {
-            const int y = i / nw, w = wlo + (i - y * nw);
-            const int gy = y0 - G::H + y;
-            if (gy < 0 || gy >= rows || w < 0 || w >= a.map_words) continue;
-            uint32_t bits = __ldcg(map_in + (size_t)gy * a.map_words + w);
-            while (bits) {
-                const int b = __ffs(bits) - 1;
-                bits &= bits - 1;
-                const int x = 32 * w + b - x0 + kPadX;
-                if (x < 0 || x >= G::SW) continue;
-                const int pos = atomicAdd(&s_cnt[2], 1);
-                if (pos < G::kListCap) lists[G::kListCap + pos] = (uint16_t)(y * G::SW + x);
+        const size_t gt = (size_t)gridDim.x * G::kThreads, gi = (size_t)blockIdx.x * G::kThreads + tid;
+        for (size_t i = gi; i < map_size; i += gt) map_clr[i] = 0u;  // map_size is 0 without maps
+        if (a.hybrid) {
+            uint32_t* bm = a.bitmaps[set_clr];
+            const unsigned nclr = s_nclr;
+            if (nclr <= a.list_cap) {
+                const uint32_t* lst = a.lists[set_clr];
+                for (size_t i = gi; i < nclr; i += gt) {
+                    unsigned im;
+                    int y, x;
+                    unpack_entry(__ldcg(lst + i), a.xb, a.yb, im, y, x);
+                    const ImgDesc d = load_desc(a.imgs, im);
+                    bm[d.bm_off + (long long)y * d.bm_words + (x >> 5)] = 0u;
+                }
+            } else {
+                for (size_t i = gi; i < (size_t)a.bm_total; i += gt) bm[i] = 0u;
             }
         }
-        __syncthreads();
     }
 
-    unsigned cta_mask = 0;
+    unsigned cta_mask = 0;          // passes that changed a core pixel of any of this CTA's tiles
+    unsigned long long dense_px = 0;  // thread 0: core pixels of the dense passes
     const __half2 two_a = __float2half2_rn(2.f * (float)a.alpha);
     const int ys = G::R0 + warp * G::kRows;
     const int ws = G::C0 / 2 + 4 * lane;
     PassCtx<B, T> c;
     c.cand = cand;
     c.ncand = 0;
-    c.x0 = x0;
-    c.y0 = y0;
-    c.rows = rows;
-    c.cols = cols;
     c.alpha = a.alpha;
     c.evals = 0;
-    int dense_passes = 0;
-    for (int t = 0; t < np; ++t) {
-        c.in = (t & 1) ? buf1 : buf0;
-        c.out = (t & 1) ? buf0 : buf1;
-        c.list = lists + (t & 1) * G::kListCap;
-        c.nlist = &s_cnt[t % 3];
-        const uint16_t* prev = lists + ((t + 1) & 1) * G::kListCap;
-        const int nprev = s_cnt[(t + 2) % 3];
-        c.changed_core = false;
-        // Counter (t + 1) % 3 was last read at the start of pass t - 1; bitmap
-        // (t + 1) & 1 was last used in pass t - 1.
-        if (tid == 0) s_cnt[(t + 1) % 3] = 0;
-        uint32_t* mark_next = marks + ((t + 1) & 1) * G::kMarkWords;
-        for (int i = tid; i < G::kMarkWords; i += G::kThreads) mark_next[i] = 0u;
-        const bool dense = (t == 0 && !from_map) || nprev > G::kListCap || nprev * G::P > G::kListEvalMax;
-        if (dense) {
-            ++dense_passes;
-            band_dense<B, T>(c, ys, ws, lane, two_a);
-            flush_candidates<B, T>(c, lane);
-        } else {
-            list_pass<B, T>(c, prev, nprev, marks + (t & 1) * G::kMarkWords, tid);
-        }
-        if (__syncthreads_or(c.changed_core)) cta_mask |= 1u << t;
-    }
-    const uint32_t* fin = (np & 1) ? buf1 : buf0;  // I_np
-    const uint32_t* pen = (np & 1) ? buf0 : buf1;  // I_(np-1) (the loaded tile when np == 1)
-
-    // Core -> canvas bytes (and I_(np-1) -> the third canvas when asked).
-    {
-        const long long off = (long long)(kPadY + y0) * pitch + kPadX + x0;
-        uint8_t* base = dst + off;
-        uint8_t* base_prev = a.canvas[third] + coff + off;
-        constexpr int CH = G::TW / 16;
-        for (int i = tid; i < G::TH * CH; i += G::kThreads) {
-            const int r = i / CH, cc = i - r * CH;
-            const int so = (G::H + r) * G::SWW + kPadX / 2 + cc * 8;
-            const uint4* s = reinterpret_cast<const uint4*>(fin + so);
-            const uint4 p = s[0], q = s[1];
-            uint4 o;
-            o.x = h2_to_bytes(p.x, p.y);
-            o.y = h2_to_bytes(p.z, p.w);
-            o.z = h2_to_bytes(q.x, q.y);
-            o.w = h2_to_bytes(q.z, q.w);
-            *reinterpret_cast<uint4*>(base + (long long)r * pitch + cc * 16) = o;
-            if (a.write_prev) {
-                const uint4* s2 = reinterpret_cast<const uint4*>(pen + so);
-                const uint4 p2 = s2[0], q2 = s2[1];
-                o.x = h2_to_bytes(p2.x, p2.y);
-                o.y = h2_to_bytes(p2.z, p2.w);
-                o.z = h2_to_bytes(q2.x, q2.y);
-                o.w = h2_to_bytes(q2.z, q2.w);
-                *reinterpret_cast<uint4*>(base_prev + (long long)r * pitch + cc * 16) = o;
+    unsigned* queue = &ctrl->tile_next[L & 1u];
+    for (;;) {
+        if (tid == 0) {
+            const int t = (int)atomicAdd(queue, 1u);
+            s_tile = t;
+            if (t < a.ntiles) {
+                // The tile's image: from the image table, else the single
+                // image described by the arguments.
+                ImgDesc d;
+                unsigned img = 0;
+                if (a.imgs) {
+                    img = (unsigned)__ldg(a.tile_img + t);
+                    d = load_desc(a.imgs, img);
+                } else {
+                    d.off = 0;
+                    d.bm_off = 0;
+                    d.pitch = (int)a.pitch;
+                    d.rows = a.rows;
+                    d.cols = a.cols;
+                    d.tiles_x = a.tiles_x;
+                    d.tile0 = 0;
+                    d.bm_words = a.bm_words;
+                    d.user = nullptr;
+                }
+                s_d = d;
+                s_img = img;
             }
         }
-    }
-    const int nlast = s_cnt[(np - 1) % 3];
-    const uint16_t* last = lists + ((np - 1) & 1) * G::kListCap;
-    // The last pass's changed core pixels -> the global change list that the
-    // next (list) pass starts from (one global atomic per CTA); an overflowed
-    // tile list forces that pass to evaluate every pixel.
-    if (a.lists[0] != nullptr) {
-        uint32_t* glist = a.lists[0];
-        unsigned* gn = &a.ctrl->list_n[0];
-        uint32_t* gbm = a.bitmaps[0];
-        int* s_sel = s_cnt + 4;  // [0]: core entries, [1]: global base
-        if (tid == 0) s_sel[0] = 0;
         __syncthreads();
-        if (nlast <= G::kListCap) {
-            // Compact the core entries to the front of `cand` (free now).
-            uint32_t* sel = reinterpret_cast<uint32_t*>(smem + G::kCandOff);
-            for (int i = tid; i < nlast; i += G::kThreads) {
-                const int q = last[i];
-                const int y = q / G::SW, x = q - y * G::SW;
-                const int gy = y0 + y - G::H, gx = x0 + x - kPadX;
-                if (in_core_px(y, x, G::H, G::TH, G::TW) && gy < rows && gx < cols) {
-                    sel[atomicAdd(&s_sel[0], 1)] = pack_entry(img, gy, gx, a.xb, a.yb);
-                    atomicOr(gbm + bm_off + (size_t)gy * bm_words + (gx >> 5), 1u << (gx & 31));
+        if (s_tile >= a.ntiles) break;
+        const unsigned img = s_img;
+        const long long pitch = s_d.pitch, coff = s_d.off, bm_off = s_d.bm_off;
+        const int rows = s_d.rows, cols = s_d.cols, bm_words = s_d.bm_words;
+        const uint8_t* src = a.canvas[cur] + coff;
+        uint8_t* dst = a.canvas[aux] + coff;
+        const int tile = s_tile - s_d.tile0;
+        const int tx = tile % s_d.tiles_x;
+        const int ty = tile / s_d.tiles_x;
+        const int x0 = tx * G::TW, y0 = ty * G::TH;
+
+        // Tile with halo: image rows [y0 - H, y0 + TH + H), columns [x0 - 16,
+        // x0 + TW + 16); always inside the canvas.  Bytes -> fp16 pairs, into
+        // both buffers (a list pass leaves unevaluated pixels as they are in
+        // its output buffer, so that buffer must start equal to the input).
+        {
+            const uint8_t* base = src + (long long)(kPadY + y0 - G::H) * pitch + x0;
+            constexpr int CH = G::SW / 16;
+            for (int i = tid; i < G::SH * CH; i += G::kThreads) {
+                const int r = i / CH, cc = i - r * CH;
+                const uint4 v = __ldg(reinterpret_cast<const uint4*>(base + (long long)r * pitch + cc * 16));
+                uint4 lo, hi;
+                lo.x = bytes_to_h2(v.x, 0x4140u); lo.y = bytes_to_h2(v.x, 0x4342u);
+                lo.z = bytes_to_h2(v.y, 0x4140u); lo.w = bytes_to_h2(v.y, 0x4342u);
+                hi.x = bytes_to_h2(v.z, 0x4140u); hi.y = bytes_to_h2(v.z, 0x4342u);
+                hi.z = bytes_to_h2(v.w, 0x4140u); hi.w = bytes_to_h2(v.w, 0x4342u);
+                uint4* d0 = reinterpret_cast<uint4*>(buf0 + r * G::SWW + cc * 8);
+                uint4* d1 = reinterpret_cast<uint4*>(buf1 + r * G::SWW + cc * 8);
+                d0[0] = lo;
+                d0[1] = hi;
+                d1[0] = lo;
+                d1[1] = hi;
+            }
+            for (int i = tid; i < 2 * G::kMarkWords; i += G::kThreads) marks[i] = 0u;
+            if (tid < 8) s_cnt[tid] = 0;
+        }
+        __syncthreads();
+        // Pass 0's "previous pass": the pixels the previous launch's last
+        // pass changed (its map or change bitmap), listed in list 1 / counter
+        // 2.  A change set that overflowed lacks some of its bits: pass 0 is
+        // then a dense pass.
+        const bool from_map = L > 0 && (use_maps || (a.hybrid && s_nin <= a.list_cap));
+        if (from_map) {
+            const uint32_t* mp = use_maps ? map_in : a.bitmaps[set_in] + bm_off;
+            const int mw = use_maps ? a.map_words : bm_words;
+            const int wlo = (x0 - kPadX) >> 5;  // floor division (x0 - 16 >= -16)
+            const int nw = ((x0 + G::TW + kPadX - 1) >> 5) - wlo + 1;
+            for (int i = tid; i < G::SH * nw; i += G::kThreads) {
+                const int y = i / nw, w = wlo + (i - y * nw);
+                const int gy = y0 - G::H + y;
+                if (gy < 0 || gy >= rows || w < 0 || w >= mw) continue;
+                uint32_t bits = __ldcg(mp + (size_t)gy * mw + w);
+                while (bits) {
+                    const int b = __ffs(bits) - 1;
+                    bits &= bits - 1;
+                    const int x = 32 * w + b - x0 + kPadX;
+                    if (x < 0 || x >= G::SW) continue;
+                    const int pos = atomicAdd(&s_cnt[2], 1);
+                    if (pos < G::kListCap) lists[G::kListCap + pos] = (uint16_t)(y * G::SW + x);
                 }
             }
             __syncthreads();
-            const int nsel = s_sel[0];
-            if (tid == 0) s_sel[1] = nsel ? (int)atomicAdd(gn, (unsigned)nsel) : 0;
-            __syncthreads();
-            const unsigned gbase = (unsigned)s_sel[1];
-            for (int i = tid; i < nsel; i += G::kThreads)
-                if (gbase + i < a.list_cap) glist[gbase + i] = sel[i];
-        } else if (tid == 0) {
-            atomicAdd(gn, a.list_cap + 1u);  // overflow: the next pass evaluates every pixel
         }
-    }
-    // The last pass's changed core pixels -> this launch's map (all core
-    // pixels when the list overflowed: a superset is always safe).
-    if (use_maps) {
-        if (nlast <= G::kListCap) {
-            for (int i = tid; i < nlast; i += G::kThreads) {
-                const int q = last[i];
-                const int y = q / G::SW, x = q - y * G::SW;
-                if (!in_core_px(y, x, G::H, G::TH, G::TW)) continue;
-                const int gy = y0 + y - G::H, gx = x0 + x - kPadX;
-                if (gy >= rows || gx >= cols) continue;
-                atomicOr(map_out + (size_t)gy * a.map_words + (gx >> 5), 1u << (gx & 31));
+
+        unsigned tile_mask = 0;
+        c.x0 = x0;
+        c.y0 = y0;
+        c.rows = rows;
+        c.cols = cols;
+        int dense_passes = 0;
+        for (int t = 0; t < np; ++t) {
+            c.in = (t & 1) ? buf1 : buf0;
+            c.out = (t & 1) ? buf0 : buf1;
+            c.list = lists + (t & 1) * G::kListCap;
+            c.nlist = &s_cnt[t % 3];
+            const uint16_t* prev = lists + ((t + 1) & 1) * G::kListCap;
+            const int nprev = s_cnt[(t + 2) % 3];
+            c.changed_core = false;
+            // Counter (t + 1) % 3 was last read at the start of pass t - 1;
+            // bitmap (t + 1) & 1 was last used in pass t - 1.
+            if (tid == 0) s_cnt[(t + 1) % 3] = 0;
+            uint32_t* mark_next = marks + ((t + 1) & 1) * G::kMarkWords;
+            for (int i = tid; i < G::kMarkWords; i += G::kThreads) mark_next[i] = 0u;
+            const bool dense = (t == 0 && !from_map) || nprev > G::kListCap || nprev * G::P > G::kListEvalMax;
+            if (dense) {
+                ++dense_passes;
+                band_dense<B, T>(c, ys, ws, lane, two_a);
+                flush_candidates<B, T>(c, lane);
+            } else {
+                list_pass<B, T>(c, prev, nprev, marks + (t & 1) * G::kMarkWords, tid);
             }
-        } else {
-            for (int r = tid; r < G::TH; r += G::kThreads) {
-                const int gy = y0 + r;
-                if (gy >= rows) break;
-                uint32_t* row = map_out + (size_t)gy * a.map_words;
-                for (int gx = x0; gx < x0 + G::TW; gx += 32 - (gx & 31)) {
-                    const int n = min(32 - (gx & 31), x0 + G::TW - gx);
-                    const uint32_t m = (n == 32 ? 0xffffffffu : ((1u << n) - 1u)) << (gx & 31);
-                    atomicOr(row + (gx >> 5), m);
+            if (__syncthreads_or(c.changed_core)) tile_mask |= 1u << t;
+        }
+        const uint32_t* fin = (np & 1) ? buf1 : buf0;  // I_np
+        const uint32_t* pen = (np & 1) ? buf0 : buf1;  // I_(np-1) (the loaded tile when np == 1)
+
+        // Core -> canvas bytes (and I_(np-1) -> the third canvas when asked).
+        {
+            const long long off = (long long)(kPadY + y0) * pitch + kPadX + x0;
+            uint8_t* base = dst + off;
+            uint8_t* base_prev = a.canvas[third] + coff + off;
+            constexpr int CH = G::TW / 16;
+            for (int i = tid; i < G::TH * CH; i += G::kThreads) {
+                const int r = i / CH, cc = i - r * CH;
+                const int so = (G::H + r) * G::SWW + kPadX / 2 + cc * 8;
+                const uint4* s = reinterpret_cast<const uint4*>(fin + so);
+                const uint4 p = s[0], q = s[1];
+                uint4 o;
+                o.x = h2_to_bytes(p.x, p.y);
+                o.y = h2_to_bytes(p.z, p.w);
+                o.z = h2_to_bytes(q.x, q.y);
+                o.w = h2_to_bytes(q.z, q.w);
+                *reinterpret_cast<uint4*>(base + (long long)r * pitch + cc * 16) = o;
+                if (a.write_prev) {
+                    const uint4* s2 = reinterpret_cast<const uint4*>(pen + so);
+                    const uint4 p2 = s2[0], q2 = s2[1];
+                    o.x = h2_to_bytes(p2.x, p2.y);
+                    o.y = h2_to_bytes(p2.z, p2.w);
+                    o.z = h2_to_bytes(q2.x, q2.y);
+                    o.w = h2_to_bytes(q2.z, q2.w);
+                    *reinterpret_cast<uint4*>(base_prev + (long long)r * pitch + cc * 16) = o;
                 }
             }
         }
+        const int nlast = s_cnt[(np - 1) % 3];
+        const uint16_t* last = lists + ((np - 1) & 1) * G::kListCap;
+        // The last pass's changed core pixels -> this launch's change set
+        // (one global atomic per tile); an overflowed tile list marks the
+        // set as overflowed, so the next pass evaluates every pixel.
+        if (a.hybrid) {
+            uint32_t* glist = a.lists[set_out];
+            unsigned* gn = &ctrl->list_n[set_out];
+            uint32_t* gbm = a.bitmaps[set_out];
+            int* s_sel = s_cnt + 4;  // [0]: core entries, [1]: global base
+            if (nlast <= G::kListCap) {
+                // Compact the core entries to the front of `cand` (free now).
+                uint32_t* sel = reinterpret_cast<uint32_t*>(smem + G::kCandOff);
+                for (int i = tid; i < nlast; i += G::kThreads) {
+                    const int q = last[i];
+                    const int y = q / G::SW, x = q - y * G::SW;
+                    const int gy = y0 + y - G::H, gx = x0 + x - kPadX;
+                    if (in_core_px(y, x, G::H, G::TH, G::TW) && gy < rows && gx < cols) {
+                        sel[atomicAdd(&s_sel[0], 1)] = pack_entry(img, gy, gx, a.xb, a.yb);
+                        atomicOr(gbm + bm_off + (size_t)gy * bm_words + (gx >> 5), 1u << (gx & 31));
+                    }
+                }
+                __syncthreads();
+                const int nsel = s_sel[0];
+                if (tid == 0) s_sel[1] = nsel ? (int)atomicAdd(gn, (unsigned)nsel) : 0;
+                __syncthreads();
+                const unsigned gbase = (unsigned)s_sel[1];
+                for (int i = tid; i < nsel; i += G::kThreads)
+                    if (gbase + i < a.list_cap) glist[gbase + i] = sel[i];
+            } else if (tid == 0) {
+                atomicAdd(gn, a.list_cap + 1u);  // overflow: the next pass evaluates every pixel
+            }
+        }
+        // The last pass's changed core pixels -> this launch's map (all core
+        // pixels when the list overflowed: a superset is always safe).
+        if (use_maps) {
+            if (nlast <= G::kListCap) {
+                for (int i = tid; i < nlast; i += G::kThreads) {
+                    const int q = last[i];
+                    const int y = q / G::SW, x = q - y * G::SW;
+                    if (!in_core_px(y, x, G::H, G::TH, G::TW)) continue;
+                    const int gy = y0 + y - G::H, gx = x0 + x - kPadX;
+                    if (gy >= rows || gx >= cols) continue;
+                    atomicOr(map_out + (size_t)gy * a.map_words + (gx >> 5), 1u << (gx & 31));
+                }
+            } else {
+                for (int r = tid; r < G::TH; r += G::kThreads) {
+                    const int gy = y0 + r;
+                    if (gy >= rows) break;
+                    uint32_t* row = map_out + (size_t)gy * a.map_words;
+                    for (int gx = x0; gx < x0 + G::TW; gx += 32 - (gx & 31)) {
+                        const int n = min(32 - (gx & 31), x0 + G::TW - gx);
+                        const uint32_t m = (n == 32 ? 0xffffffffu : ((1u << n) - 1u)) << (gx & 31);
+                        atomicOr(row + (gx >> 5), m);
+                    }
+                }
+            }
+        }
+        if (tid == 0) {
+            // Dense passes evaluate every core pixel on the image.
+            const int ch = min(G::TH, rows - y0), cw = min(G::TW, cols - x0);
+            dense_px += (unsigned long long)dense_passes * (unsigned long long)(ch * cw);
+            // Image k: the image changed in passes 1 .. (highest set bit).
+            if (a.img_k && tile_mask) atomicMax(a.img_k + img, s_k + 32u - (unsigned)__clz(tile_mask));
+        }
+        cta_mask |= tile_mask;
+        __syncthreads();  // the next tile reuses shared memory
     }
-    // Work accounting (one global atomic per CTA): dense passes evaluate
-    // every core pixel on the image.
+    // Work accounting (one global atomic per CTA).
     {
-        int* s_ev = s_cnt + 6;
-        if (tid == 0) s_ev[0] = 0;
+        __shared__ unsigned long long s_ev;
+        if (tid == 0) s_ev = dense_px;
         __syncthreads();
         const unsigned ev = __reduce_add_sync(0xffffffffu, c.evals);
-        if (lane == 0 && ev) atomicAdd(&s_ev[0], (int)ev);
+        if (lane == 0 && ev) atomicAdd(&s_ev, (unsigned long long)ev);
         __syncthreads();
-        if (tid == 0) {
-            const int ch = min(G::TH, rows - y0), cw = min(G::TW, cols - x0);
-            const unsigned long long total =
-                (unsigned long long)s_ev[0] + (unsigned long long)dense_passes * (unsigned long long)(ch * cw);
-            if (total) atomicAdd(&a.ctrl->evals_fused, total);
+        if (tid == 0 && s_ev) atomicAdd(&ctrl->evals_fused, s_ev);
+    }
+    if (tid == 0) {
+        const bool last_cta = finish_launch(ctrl, cta_mask, np, gridDim.x, aux, a.write_prev ? third : cur);
+        if (last_cta) {
+            ctrl->fused_work += 1u;
+            ctrl->tile_next[(L + 1u) & 1u] = 0u;  // the queue of the next fused launch
+            if (a.hybrid) {
+                ctrl->list_n[set_clr] = 0u;  // cleared above; every CTA has read its count
+                // Would a list pass evaluate more than relaunch_evals pixels?
+                const unsigned long long nout = ctrl->list_n[set_out];
+                ctrl->dense = (nout > a.list_cap || nout * (unsigned long long)G::P > (unsigned long long)a.relaunch_evals)
+                                  ? 1u : 0u;
+            }
+            __threadfence();
         }
     }
-    // Image k: the image changed in passes 1 .. (highest set bit of the mask).
-    if (tid == 0 && a.img_k && cta_mask) atomicMax(a.img_k + img, s_k + 32u - (unsigned)__clz(cta_mask));
-    if (tid == 0) finish_launch(a.ctrl, cta_mask, np, gridDim.x, aux, a.write_prev ? third : cur);
 }
 
 // Host-side description of one compiled (beta, T) instance.
@@ -674,10 +739,28 @@ struct FusedEntry {
 template <int B, int T>
 cudaError_t launch_fused(const PassArgs& a, int ctas, cudaStream_t s) {
     using G = FusedGeo<B, T>;
-    cudaError_t e = cudaFuncSetAttribute(fused_kernel<B, T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)G::kSmem);
+    // Per device: resident CTAs per SM and SM count (set up on first use).
+    constexpr int kMaxDev = 64;
+    static int occ[kMaxDev] = {};
+    static int sms[kMaxDev] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
-    fused_kernel<B, T><<<(unsigned)ctas, G::kThreads, G::kSmem, s>>>(a);
+    if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
+    if (occ[dev] == 0) {
+        e = cudaFuncSetAttribute(fused_kernel<B, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::kSmem);
+        int n = 0, o = 0;
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e == cudaSuccess)
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fused_kernel<B, T>, G::kThreads, G::kSmem);
+        if (e != cudaSuccess) return e;
+        if (o < 1) return cudaErrorInvalidConfiguration;
+        sms[dev] = n;
+        occ[dev] = o;
+    }
+    const long long cap = (long long)sms[dev] * occ[dev];
+    const unsigned grid = (unsigned)(ctas < cap ? (ctas > 0 ? ctas : 1) : cap);
+    fused_kernel<B, T><<<grid, G::kThreads, G::kSmem, s>>>(a);
     return cudaGetLastError();
 }
 

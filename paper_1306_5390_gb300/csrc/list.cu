@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
     constexpr int W = 2 * B + 1, P = W * W;
     constexpr int kWarps = kListThreads / 32;
     __shared__ int s_np;
-    __shared__ unsigned s_k, s_cur, s_aux, s_maxk, s_gen;
+    __shared__ unsigned s_k, s_cur, s_aux, s_maxk, s_gen, s_base;
     __shared__ unsigned s_n, s_nclr;
     __shared__ uint32_t stage_all[kWarps][StagedList::kCap];
     __shared__ int s_counts[kWarps + 1];
@@ -165,12 +165,15 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
         s_aux = __ldcg(&ctrl->aux);
         s_maxk = __ldcg(&ctrl->max_k);
         s_gen = 0u;  // barriers completed; the barrier struct is zeroed at the start of every call
+        // The last fused launch wrote change set (fused launches - 1) % 4.
+        s_base = (__ldcg(&ctrl->fused_work) + 3u) & 3u;
     }
     if constexpr (kBatch)
         for (int i = tid; i < kMaxBatchImages / 32; i += kListThreads) s_imgbits[i] = 0u;
     __syncthreads();
     if (s_np == 0) return;  // the fused launch already finished the call
     unsigned k = s_k, cur = s_cur, aux = s_aux, gen = s_gen;
+    const int base = (int)s_base;
     const unsigned max_k = s_maxk;
     bool converged = false, failed = false;
     int passes = 0;
@@ -196,7 +199,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
     StagedList sl{stage_all[warp], 0};
 
     for (int t = 0; k < max_k; ++t) {
-        const int si = t & 3, so = (t + 1) & 3, sc = (t + 3) & 3;
+        const int si = (t + base) & 3, so = (t + base + 1) & 3, sc = (t + base + 3) & 3;
         const uint8_t* in_arena = a.canvas[cur];
         uint8_t* out_arena = a.canvas[aux];
         const uint32_t* prev = a.lists[si];
@@ -208,9 +211,9 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
             s_n = __ldcg(&ctrl->list_n[si]);
             s_nclr = __ldcg(&ctrl->list_n[sc]);
             if (blockIdx.x == 0) {
-                // Set (t + 2) % 4 is next written by pass t + 1; its list was
-                // last read (to clear its bitmap) in pass t - 1.
-                ctrl->list_n[(t + 2) & 3] = 0u;
+                // Set (t + base + 2) % 4 is next written by pass t + 1; its
+                // list was last read (to clear its bitmap) in pass t - 1.
+                ctrl->list_n[(t + base + 2) & 3] = 0u;
             }
         }
         __syncthreads();

@@ -97,6 +97,10 @@ __global__ void ctrl_init_kernel(Ctrl* c, unsigned max_k) {
     c->error = 0;
     c->evals_fused = 0;
     c->evals_list = 0;
+    c->fused_work = 0;
+    c->dense = 0;
+    c->tile_next[0] = 0;
+    c->tile_next[1] = 0;
 }
 
 cudaError_t launch_ctrl_init(Ctrl* c, unsigned max_k, cudaStream_t s) {

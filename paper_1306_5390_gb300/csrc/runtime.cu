@@ -16,6 +16,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <algorithm>
 #include <new>
 #include <vector>
 
@@ -64,6 +65,7 @@ struct hgrms_ctx {
     std::vector<hg::ImgDesc> table_cache;  // what d_desc and tile_img hold now
     int table_tiles = -1;
     int opt_batch_mb = 0;
+    int opt_relaunch_ppm = 0;
 };
 
 namespace hg {
@@ -90,6 +92,19 @@ int default_passes(int beta) {
 }  // namespace hg
 
 namespace {
+
+// Hybrid schedule: fused launches after the first (each runs only when the
+// previous one left many changed pixels; a launch that does not run still
+// costs a few microseconds).  Default: for beta 1 (T = 8, the cheapest fused
+// pass) up to 3 of them, when a list pass would evaluate more than 2.5 % of
+// the pixels (measured on GB300: list passes stay faster below that); none
+// for wider windows, whose fused passes cost more than list passes even on
+// dense change sets.  With HGRMS_OPT_RELAUNCH_PPM set, up to 8 for any beta.
+constexpr int kDefaultRelaunches = 3;
+constexpr int kMaxRelaunches = 8;
+long long default_relaunch_ppm(int beta) {
+    return beta == 1 ? 25000 : 1000000;
+}
 
 using hg::default_passes;
 using hg::find_fused;
@@ -410,15 +425,26 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
     a.tile_img = h->tile_img;
     a.bm_total = bm_total;
     a.img_k = per_image_k ? h->img_k : nullptr;
-    const int launches = max_k > 0 ? (max_k > T ? 2 : 1) : 0;
+    a.ntiles = (int)tiles_total;
+    a.hybrid = 1;
+    const bool user_ppm = h->opt_relaunch_ppm > 0;
+    const long long ppm = user_ppm ? h->opt_relaunch_ppm : default_relaunch_ppm(beta);
+    a.relaunch_evals = ppm >= 1000000 ? (1ll << 62) : px_total / 1000000 * ppm + px_total % 1000000 * ppm / 1000000;
+    const int relaunches = ppm >= 1000000 ? 0 : (user_ppm ? kMaxRelaunches : kDefaultRelaunches);
+    // Fused launches: the first always runs; each later one runs only while
+    // the previous one left many changed pixels (decided on the device).
+    // Then one launch runs every remaining pass as a list pass.
+    const int fused_launches = max_k > 0 ? std::min((max_k + T - 1) / T, 1 + relaunches) : 0;
+    const bool list_loop = max_k > T;
+    const int launches = fused_launches + (list_loop ? 1 : 0);
     const bool timed = h->opt_timing != 0;
     if (timed) {
-        rc = ensure_events(h, 4);
+        rc = ensure_events(h, 2 * (size_t)launches);
         if (rc < 0) return rc;
     }
     for (int i = 0; i < launches; ++i) {
         if (timed) HG_TRY(h, cudaEventRecord(h->events[2 * i], s));
-        if (i == 0)
+        if (i < fused_launches)
             HG_TRY(h, fe->launch(a, (int)tiles_total, s));
         else
             HG_TRY(h, hg::launch_list(beta, a, h->sms, s));
@@ -446,12 +472,16 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
     }
     if (host_out) HG_TRY(h, cudaStreamSynchronize(s));
     if (timed) {
+        // Fused launches that ran passes come first; the list-pass launch
+        // ran passes when work_launches counts it.
+        const bool list_worked = c.work_launches > c.fused_work;
         for (int i = 0; i < launches; ++i) {
             float ms = 0.f;
             HG_TRY(h, cudaEventElapsedTime(&ms, h->events[2 * i], h->events[2 * i + 1]));
+            const bool worked = i < fused_launches ? i < (int)c.fused_work : list_worked;
             h->launch_ms.push_back(ms);
-            h->launch_kind.push_back(i == 0 ? 0 : 1);
-            if (i < (int)c.work_launches)
+            h->launch_kind.push_back(worked ? (i < fused_launches ? 0 : 1) : 3);
+            if (worked)
                 h->stats.kernel_ms += ms;
             else
                 h->stats.idle_kernel_ms += ms;
@@ -535,6 +565,9 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     a.tile_img = nullptr;
     a.bm_total = 0;
     a.img_k = nullptr;
+    a.ntiles = p.tiles_x * p.tiles_y;
+    a.hybrid = 0;
+    a.relaunch_evals = 0;
     // Per-launch timing is limited to calls of at most kMaxTimedLaunches launches.
     constexpr int kMaxTimedLaunches = 4096;
     const bool timed = h->opt_timing && p.launches <= kMaxTimedLaunches;
@@ -576,7 +609,7 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
             float ms = 0.f;
             HG_TRY(h, cudaEventElapsedTime(&ms, h->events[2 * i], h->events[2 * i + 1]));
             h->launch_ms.push_back(ms);
-            h->launch_kind.push_back(i < p.fused_launches ? 0 : (p.fused ? 1 : 2));
+            h->launch_kind.push_back(i < (int)c.work_launches ? (p.fused ? 0 : 2) : 3);
             if (i < (int)c.work_launches)
                 h->stats.kernel_ms += ms;
             else
@@ -789,6 +822,10 @@ HG_EXPORT int hgrms_set_option(hgrms_t h, int option, int value) {
         case HGRMS_OPT_BATCH_MB:
             if (value < 0) return HGRMS_EINVAL;
             h->opt_batch_mb = value;
+            return HGRMS_OK;
+        case HGRMS_OPT_RELAUNCH_PPM:
+            if (value < 0) return HGRMS_EINVAL;
+            h->opt_relaunch_ppm = value;
             return HGRMS_OK;
         default: return HGRMS_EINVAL;
     }

@@ -31,6 +31,7 @@ HGRMS_OPT_PASSES = 2
 HGRMS_OPT_TIMING = 3
 HGRMS_OPT_LIST_CAP = 4
 HGRMS_OPT_BATCH_MB = 5
+HGRMS_OPT_RELAUNCH_PPM = 6
 
 # Every symbol the header declares (the CPU tests check the library exports them).
 EXPORTED = (
@@ -180,7 +181,7 @@ def hgrms_stats(h) -> dict:
 
 
 def hgrms_launch_times(h):
-    """[(ms, kind)] per launch of the last call (kind 0 fused, 1 list, 2 unfused)."""
+    """[(ms, kind)] per launch of the last call (kind 0 fused, 1 list, 2 unfused, 3 ran no pass)."""
     lib = load_library()
     n = lib.hgrms_launch_times(h, None, None, 0)
     if n < 0:

@@ -56,6 +56,7 @@ def run_batch(den, torch, imgs, alpha, beta, max_k, host=False, **opts):
     den.set_option(hgrms.HGRMS_OPT_PASSES, opts.get("passes", 0))
     den.set_option(hgrms.HGRMS_OPT_LIST_CAP, opts.get("list_cap", 0))
     den.set_option(hgrms.HGRMS_OPT_BATCH_MB, opts.get("batch_mb", 0))
+    den.set_option(hgrms.HGRMS_OPT_RELAUNCH_PPM, opts.get("relaunch_ppm", 0))
     if host:
         work = [np.ascontiguousarray(im).copy() for im in imgs]
         ks = den.denoise_batch(work, alpha, beta, max_k)
@@ -65,7 +66,8 @@ def run_batch(den, torch, imgs, alpha, beta, max_k, host=False, **opts):
         ks = den.denoise_batch(work, alpha, beta, max_k)
         outs = [t.cpu().numpy() for t in work]
     conv = den.converged()
-    for opt in (hgrms.HGRMS_OPT_PASSES, hgrms.HGRMS_OPT_LIST_CAP, hgrms.HGRMS_OPT_BATCH_MB):
+    for opt in (hgrms.HGRMS_OPT_PASSES, hgrms.HGRMS_OPT_LIST_CAP, hgrms.HGRMS_OPT_BATCH_MB,
+                hgrms.HGRMS_OPT_RELAUNCH_PPM):
         den.set_option(opt, 0)
     return outs, ks, conv
 
@@ -184,3 +186,16 @@ def test_uneven_workload_slice_full_size(oracle_mod, den, torch_cuda):
     imgs = [w["noisy"] for w in synth.workload_batch(512, first=0, last=6)]
     outs, ks, conv = run_batch(den, torch_cuda, imgs, 10, 1, 32)
     check(oracle_mod, imgs, outs, ks, conv, 10, 1, 32, "uneven")
+
+
+@pytest.mark.parametrize("beta,passes,max_k,list_cap", [(1, 0, 32, 0), (1, 3, 32, 0), (2, 0, 32, 0), (3, 0, 13, 0),
+                                                      (1, 0, 32, 40), (2, 2, 32, 40), (1, 1, 20, 0)])
+def test_fused_relaunches_in_batch(oracle_mod, den, torch_cuda, beta, passes, max_k, list_cap):
+    """A threshold of 1 pixel per million makes every fused launch after the
+    first run while anything changed (up to 8 of them), with list passes for
+    what is left; with a small list capacity some change sets overflow, so
+    the next fused launch starts with a dense pass."""
+    imgs = mixed_batch(14, 900 + 10 * beta + passes + list_cap)
+    outs, ks, conv = run_batch(den, torch_cuda, imgs, 10, beta, max_k, passes=passes, list_cap=list_cap,
+                               relaunch_ppm=1)
+    check(oracle_mod, imgs, outs, ks, conv, 10, beta, max_k, f"relaunch b={beta} T={passes} cap={list_cap}")

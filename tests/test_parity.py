@@ -36,11 +36,12 @@ def den(torch_cuda):
     d.close()
 
 
-def gpu_denoise(d, torch, img, alpha, beta, max_k, passes=0, kernel=0, host=False, list_cap=0):
+def gpu_denoise(d, torch, img, alpha, beta, max_k, passes=0, kernel=0, host=False, list_cap=0, relaunch_ppm=0):
     from paper_1306_5390_gb300 import hgrms
     d.set_option(hgrms.HGRMS_OPT_PASSES, passes)
     d.set_option(hgrms.HGRMS_OPT_KERNEL, kernel)
     d.set_option(hgrms.HGRMS_OPT_LIST_CAP, list_cap)
+    d.set_option(hgrms.HGRMS_OPT_RELAUNCH_PPM, relaunch_ppm)
     if host:
         out = np.ascontiguousarray(img).copy()
         k = d.denoise(out, alpha, beta, max_k)
@@ -123,6 +124,18 @@ def test_list_overflow_falls_back_to_full_pass(oracle_mod, den, torch_cuda, list
         _, noisy = synth.noisy_image(150, 333, 0.4, synth.seed_for(31, beta))
         for passes in (1, 2):
             assert_same(oracle_mod, den, torch_cuda, noisy, 10, beta, 32, passes=passes, list_cap=list_cap)
+
+
+@pytest.mark.parametrize("beta,passes", [(1, 8), (1, 2), (2, 4), (3, 2), (4, 1)])
+@pytest.mark.parametrize("ppm", [1, 5000])
+def test_fused_relaunches(oracle_mod, den, torch_cuda, beta, passes, ppm):
+    """Relaunch thresholds that make later fused launches run (every one
+    while pixels change, or while more than 0.5 % would be evaluated)."""
+    for i, (r, c) in enumerate([(301, 517), (64, 1000), (530, 250)]):
+        _, noisy = synth.noisy_image(r, c, 0.45, synth.seed_for(31, 10 * beta + i))
+        assert_same(oracle_mod, den, torch_cuda, noisy, 10, beta, 32, passes=passes, relaunch_ppm=ppm)
+    _, noisy = synth.noisy_image(200, 300, 0.6, synth.seed_for(32, beta))
+    assert_same(oracle_mod, den, torch_cuda, noisy, 10, beta, 32, passes=passes, relaunch_ppm=1, list_cap=30)
 
 
 def test_unfused_kernel_every_beta(oracle_mod, den, torch_cuda):
