@@ -151,6 +151,16 @@ int hgrms_denoise_noalloc(uint8_t* img, int rows, int cols, int alpha, int beta,
                                     this many pixels per million pixels of the call, up to 8 times
                                     (0 = built-in: 25000 for beta 1, up to 3 times, never for
                                     beta >= 2; 1000000 or more = never) */
+#define HGRMS_OPT_AUTOTUNE 8 /* 1 = choose the fused passes per launch and the in-tile switch point
+                                 by timing: the first call of each (beta, single image or batch,
+                                 size class = bit length of the pixel count) runs every compiled
+                                 passes-per-launch value with switch points 1024..8192 on its own
+                                 images, without writing them, and keeps the fastest; the result does
+                                 not depend on the choice.  Options 2 and 7, when set, are kept. */
+#define HGRMS_OPT_TILE_EVAL_MAX 7 /* fused kernel: a pass runs as an in-tile list pass while the previous
+                                     pass's changes need at most this many evaluations in the tile,
+                                     else as a dense pass (0 = built-in: 2048 for beta 2, else
+                                     4096) */
 
 /* Set an option.  Returns HGRMS_OK or HGRMS_EINVAL (unknown option or value,
  * e.g. a pass count that has no compiled kernel for some beta is rejected at
@@ -176,6 +186,10 @@ typedef struct hgrms_stats {
                                (every image pixel per dense pass, else the pixels within
                                beta of a change of the previous pass) */
     long long evals_list;   /* the same for list-pass launches */
+    int    tile_eval_max;   /* in-tile list/dense switch point used (HGRMS_OPT_TILE_EVAL_MAX) */
+    int    autotuned;       /* 1 if the tuning came from the autotuner (HGRMS_OPT_AUTOTUNE) */
+    double tune_ms;         /* device time the autotuner's trials took in this call (0 when the
+                               choice was already known) */
 } hgrms_stats_t;
 
 int hgrms_stats(hgrms_t h, hgrms_stats_t* out);

@@ -147,6 +147,10 @@ struct PassArgs {
     // the last fused launch's set.
     int hybrid;
     long long relaunch_evals;
+    // Fused kernel: a pass runs as an in-tile list pass when the previous
+    // pass's changes need at most this many pixel evaluations in the tile
+    // (0 = the kernel's built-in value), else as a dense pass.
+    int tile_eval_max;
 };
 
 // Passes the launch must run: 0 when the call has finished.

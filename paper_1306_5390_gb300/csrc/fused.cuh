@@ -73,7 +73,7 @@ struct FusedGeo {
     static constexpr int P = (2 * B + 1) * (2 * B + 1);
     static constexpr int kCandCap = kRows / 2 * 256;  // per-warp candidate list (half a band)
     static constexpr int kListCap = 2048;            // changed pixels kept per pass
-    static constexpr int kListEvalMax = 2048;        // list-pass evaluations above which a pass runs dense
+    static constexpr int kListEvalMax = 2048;        // default: list-pass evaluations above which a pass runs dense
     static constexpr int kMarkWords = (SH * SW + 31) / 32;
     // shared memory layout (bytes)
     static constexpr size_t kBufBytes = (size_t)SH * SW * sizeof(__half);
@@ -482,6 +482,7 @@ fused_kernel(PassArgs a) {
     c.alpha = a.alpha;
     c.evals = 0;
     unsigned* queue = &ctrl->tile_next[L & 1u];
+    const int eval_max = a.tile_eval_max > 0 ? a.tile_eval_max : G::kListEvalMax;
     for (;;) {
         if (tid == 0) {
             const int t = (int)atomicAdd(queue, 1u);
@@ -593,7 +594,7 @@ fused_kernel(PassArgs a) {
             if (tid == 0) s_cnt[(t + 1) % 3] = 0;
             uint32_t* mark_next = marks + ((t + 1) & 1) * G::kMarkWords;
             for (int i = tid; i < G::kMarkWords; i += G::kThreads) mark_next[i] = 0u;
-            const bool dense = (t == 0 && !from_map) || nprev > G::kListCap || nprev * G::P > G::kListEvalMax;
+            const bool dense = (t == 0 && !from_map) || nprev > G::kListCap || nprev * G::P > eval_max;
             if (dense) {
                 ++dense_passes;
                 band_dense<B, T>(c, ys, ws, lane, two_a);

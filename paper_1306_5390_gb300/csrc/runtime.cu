@@ -17,6 +17,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <algorithm>
+#include <map>
 #include <new>
 #include <vector>
 
@@ -25,6 +26,12 @@
 #include "kernels.h"
 
 #define HG_EXPORT extern "C" __attribute__((visibility("default")))
+
+// Fused passes per launch and in-tile list/dense switch point of one call.
+struct Tuning {
+    int T;
+    int eval_max;
+};
 
 struct hgrms_ctx {
     int device = 0;
@@ -66,6 +73,10 @@ struct hgrms_ctx {
     int table_tiles = -1;
     int opt_batch_mb = 0;
     int opt_relaunch_ppm = 0;
+    int opt_tile_eval_max = 0;
+    int opt_autotune = 0;
+    std::map<long long, Tuning> tuned;  // autotuner choices by (beta, batch, size class)
+    cudaEvent_t tune_ev[2] = {nullptr, nullptr};
 };
 
 namespace hg {
@@ -305,6 +316,11 @@ struct BatchImg {
     bool dev;  // device memory of the handle's device (else host memory)
 };
 
+// Built-in in-tile list/dense switch point per beta (measured on GB300).
+int default_eval_max(int beta) {
+    return beta == 2 ? 2048 : 4096;
+}
+
 // Canvas, bitmap and list bytes the hybrid schedule needs for one image (a
 // chunk needs the sum, plus a small constant).
 long long hybrid_bytes(const hg::FusedEntry* fe, int rows, int cols) {
@@ -323,8 +339,13 @@ long long hybrid_bytes(const hg::FusedEntry* fe, int rows, int cols) {
 // after max_k passes, and image i's k is the number of the last pass that
 // changed one of its pixels (an image that a pass leaves unchanged is at a
 // fixed point, so later passes leave it unchanged too).
-int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int max_k, int* k_out) {
-    const int T = h->opt_passes > 0 ? h->opt_passes : default_passes(beta);
+//
+// `tu` gives the fused passes per launch and the in-tile list/dense switch
+// point.  With write_back false the images are not written (an autotuning
+// trial); *ms, when given, receives the device time of the call's work.
+int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int max_k, int* k_out,
+               const Tuning& tu, bool write_back, float* ms) {
+    const int T = tu.T;
     const hg::FusedEntry* fe = find_fused(beta, T);
     if (!fe) return HGRMS_EINVAL;
     const bool per_image_k = n > 1;
@@ -382,6 +403,7 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
         h->table_cache.assign(h->host_desc, h->host_desc + n);
         h->table_tiles = (int)tiles_total;
     }
+    if (ms) HG_TRY(h, cudaEventRecord(h->tune_ev[0], s));
     // Images in: device images by kernel, host images by 2-D copies.
     if (n == 1 && im[0].dev) {
         HG_TRY(h, hg::launch_copy_in(im[0].ptr, im[0].rows, im[0].cols, h->canvas[0], h->host_desc[0].pitch, h->sms, s));
@@ -427,6 +449,7 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
     a.img_k = per_image_k ? h->img_k : nullptr;
     a.ntiles = (int)tiles_total;
     a.hybrid = 1;
+    a.tile_eval_max = tu.eval_max;
     const bool user_ppm = h->opt_relaunch_ppm > 0;
     const long long ppm = user_ppm ? h->opt_relaunch_ppm : default_relaunch_ppm(beta);
     a.relaunch_evals = ppm >= 1000000 ? (1ll << 62) : px_total / 1000000 * ppm + px_total % 1000000 * ppm / 1000000;
@@ -450,19 +473,22 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
             HG_TRY(h, hg::launch_list(beta, a, h->sms, s));
         if (timed) HG_TRY(h, cudaEventRecord(h->events[2 * i + 1], s));
     }
-    if (n == 1 && im[0].dev) {
+    if (!write_back) {
+        // trial: no copy-out
+    } else if (n == 1 && im[0].dev) {
         HG_TRY(h, hg::launch_copy_out(h->ctrl, h->canvas, h->host_desc[0].pitch, im[0].ptr, im[0].rows, im[0].cols,
                                       h->sms, s));
     } else {
         HG_TRY(h, hg::launch_copy_out_batch(h->ctrl, h->canvas, h->d_desc, n, max_words, h->sms, s));
     }
+    if (ms) HG_TRY(h, cudaEventRecord(h->tune_ev[1], s));
     HG_TRY(h, cudaMemcpyAsync(h->host_ctrl, h->ctrl, sizeof(hg::Ctrl), cudaMemcpyDeviceToHost, s));
     if (per_image_k)
         HG_TRY(h, cudaMemcpyAsync(h->host_img_k, h->img_k, (size_t)n * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     HG_TRY(h, cudaStreamSynchronize(s));
     const hg::Ctrl c = *h->host_ctrl;
     bool host_out = false;
-    for (int i = 0; i < n; ++i) {
+    for (int i = 0; i < n && write_back; ++i) {
         if (im[i].dev) continue;
         const hg::ImgDesc& d = h->host_desc[i];
         HG_TRY(h, cudaMemcpy2DAsync(im[i].ptr, (size_t)d.cols,
@@ -471,6 +497,7 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
         host_out = true;
     }
     if (host_out) HG_TRY(h, cudaStreamSynchronize(s));
+    if (ms) HG_TRY(h, cudaEventElapsedTime(ms, h->tune_ev[0], h->tune_ev[1]));
     if (timed) {
         // Fused launches that ran passes come first; the list-pass launch
         // ran passes when work_launches counts it.
@@ -494,6 +521,7 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
     for (int i = 0; i < n; ++i) k_out[i] = per_image_k ? (int)h->host_img_k[i] : (int)c.k;
     h->stats.launches += launches;
     h->stats.passes_per_launch = T;
+    h->stats.tile_eval_max = tu.eval_max;
     h->stats.tile_rows = fe->TH;
     h->stats.tile_cols = fe->TW;
     h->stats.ctas_per_launch += tiles_total;
@@ -503,6 +531,72 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
     h->stats.work_launches += (int)c.work_launches;
     h->stats.passes += (int)(c.k + c.converged);
     h->converged = (int)c.converged;
+    return HGRMS_OK;
+}
+
+// The tuning of a hybrid call: the options when set, else the autotuner's
+// choice for (beta, single image or batch, size class) when autotuning is on
+// (the first call of a class times every compiled T with four switch points
+// on the call's own images, which are not written by the trials, and keeps
+// the fastest; every candidate gives the same result), else the built-in
+// values.
+int choose_tuning(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int max_k, int* k_scratch,
+                  Tuning* out) {
+    Tuning tu{h->opt_passes > 0 ? h->opt_passes : default_passes(beta),
+              h->opt_tile_eval_max > 0 ? h->opt_tile_eval_max : default_eval_max(beta)};
+    if (!h->opt_autotune || (h->opt_passes > 0 && h->opt_tile_eval_max > 0)) {
+        *out = tu;
+        return HGRMS_OK;
+    }
+    long long px = 0;
+    for (int i = 0; i < n; ++i) px += (long long)im[i].rows * im[i].cols;
+    const long long key = ((long long)beta << 8) | ((n > 1 ? 1ll : 0ll) << 7) | (long long)bits_for(px);
+    auto it = h->tuned.find(key);
+    if (it != h->tuned.end()) {
+        *out = it->second;
+        h->stats.autotuned = 1;
+        return HGRMS_OK;
+    }
+    std::vector<int> Ts;
+    if (h->opt_passes > 0) {
+        Ts.push_back(h->opt_passes);
+    } else {
+        for (int T = 1; T <= 32; ++T)
+            if (find_fused(beta, T)) Ts.push_back(T);
+    }
+    std::vector<int> ems;
+    if (h->opt_tile_eval_max > 0)
+        ems.push_back(h->opt_tile_eval_max);
+    else
+        ems = {1024, 2048, 4096, 8192};
+    const int reps = px < (4ll << 20) ? 3 : 1;
+    Tuning best = tu;
+    float best_ms = 3.0e38f;
+    float tune_total = 0.f;
+    for (int T : Ts)
+        for (int em : ems) {
+            const Tuning c{T, em};
+            float t_min = 3.0e38f;
+            for (int r = 0; r < reps; ++r) {
+                float ms = 0.f;
+                const int rc = run_hybrid(h, im, n, alpha, beta, max_k, k_scratch, c, false, &ms);
+                if (rc < 0) return rc;
+                tune_total += ms;
+                if (ms < t_min) t_min = ms;
+            }
+            if (t_min < best_ms) {
+                best_ms = t_min;
+                best = c;
+            }
+        }
+    h->tuned[key] = best;
+    const double tune_ms = h->stats.tune_ms + tune_total;
+    h->stats = hgrms_stats_t{};  // the trials' counts are not the call's
+    h->stats.tune_ms = tune_ms;
+    h->stats.autotuned = 1;
+    h->launch_ms.clear();
+    h->launch_kind.clear();
+    *out = best;
     return HGRMS_OK;
 }
 
@@ -568,6 +662,7 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     a.ntiles = p.tiles_x * p.tiles_y;
     a.hybrid = 0;
     a.relaunch_evals = 0;
+    a.tile_eval_max = h->opt_tile_eval_max;
     // Per-launch timing is limited to calls of at most kMaxTimedLaunches launches.
     constexpr int kMaxTimedLaunches = 4096;
     const bool timed = h->opt_timing && p.launches <= kMaxTimedLaunches;
@@ -651,6 +746,8 @@ HG_EXPORT int hgrms_create(hgrms_t* out, int device, void* cuda_stream) {
     if (e == cudaSuccess) e = cudaMalloc(&h->bar, sizeof(hg::GridBar));
     if (e == cudaSuccess) e = cudaMemset(h->ctrl, 0, sizeof(hg::Ctrl));
     if (e == cudaSuccess) e = cudaMallocHost(&h->host_ctrl, sizeof(hg::Ctrl));
+    if (e == cudaSuccess) e = cudaEventCreate(&h->tune_ev[0]);
+    if (e == cudaSuccess) e = cudaEventCreate(&h->tune_ev[1]);
     if (e != cudaSuccess) {
         rc = cuda_fail(h, e);
         hgrms_destroy(h);
@@ -679,6 +776,8 @@ HG_EXPORT void hgrms_destroy(hgrms_t h) {
         if (h->img_k) cudaFree(h->img_k);
         if (h->host_img_k) cudaFreeHost(h->host_img_k);
         for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+        for (cudaEvent_t e : h->tune_ev)
+            if (e) cudaEventDestroy(e);
     }
     delete h;
 }
@@ -696,7 +795,10 @@ HG_EXPORT int hgrms_denoise(hgrms_t h, uint8_t* img, int rows, int cols, int alp
     if (h->opt_kernel != kHybrid) return denoise_one(h, img, rows, cols, alpha, beta, max_k, kind == 1, true);
     const BatchImg bi{img, rows, cols, kind == 1};
     int k = 0;
-    rc = run_hybrid(h, &bi, 1, alpha, beta, max_k, &k);
+    Tuning tu;
+    rc = choose_tuning(h, &bi, 1, alpha, beta, max_k, &k, &tu);
+    if (rc < 0) return rc;
+    rc = run_hybrid(h, &bi, 1, alpha, beta, max_k, &k, tu, true, nullptr);
     return rc < 0 ? rc : k;
 }
 
@@ -743,7 +845,10 @@ HG_EXPORT int hgrms_denoise_batch(hgrms_t h, uint8_t* const* imgs, const int* ro
                 mc = mc2;
                 ++end;
             }
-            const int rc = run_hybrid(h, bi.data() + start, end - start, alpha, beta, max_k, k_out + start);
+            Tuning tu;
+            int rc = choose_tuning(h, bi.data() + start, end - start, alpha, beta, max_k, k_out + start, &tu);
+            if (rc < 0) return rc;
+            rc = run_hybrid(h, bi.data() + start, end - start, alpha, beta, max_k, k_out + start, tu, true, nullptr);
             if (rc < 0) return rc;
             start = end;
         }
@@ -826,6 +931,14 @@ HG_EXPORT int hgrms_set_option(hgrms_t h, int option, int value) {
         case HGRMS_OPT_RELAUNCH_PPM:
             if (value < 0) return HGRMS_EINVAL;
             h->opt_relaunch_ppm = value;
+            return HGRMS_OK;
+        case HGRMS_OPT_AUTOTUNE:
+            if (value != 0 && value != 1) return HGRMS_EINVAL;
+            h->opt_autotune = value;
+            return HGRMS_OK;
+        case HGRMS_OPT_TILE_EVAL_MAX:
+            if (value < 0 || value > (1 << 20)) return HGRMS_EINVAL;
+            h->opt_tile_eval_max = value;
             return HGRMS_OK;
         default: return HGRMS_EINVAL;
     }

@@ -32,6 +32,8 @@ HGRMS_OPT_TIMING = 3
 HGRMS_OPT_LIST_CAP = 4
 HGRMS_OPT_BATCH_MB = 5
 HGRMS_OPT_RELAUNCH_PPM = 6
+HGRMS_OPT_TILE_EVAL_MAX = 7
+HGRMS_OPT_AUTOTUNE = 8
 
 # Every symbol the header declares (the CPU tests check the library exports them).
 EXPORTED = (
@@ -56,6 +58,9 @@ class hgrms_stats_t(ctypes.Structure):
         ("idle_kernel_ms", ctypes.c_double),
         ("evals_fused", ctypes.c_longlong),
         ("evals_list", ctypes.c_longlong),
+        ("tile_eval_max", ctypes.c_int),
+        ("autotuned", ctypes.c_int),
+        ("tune_ms", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -206,11 +211,12 @@ class Denoiser:
     """Owns one library handle (one device, one stream)."""
 
     def __init__(self, device: int = 0, cuda_stream: int | None = None, kernel: int = 0,
-                 passes: int = 0, timing: bool = False):
+                 passes: int = 0, timing: bool = False, autotune: bool = False):
         self.h = hgrms_create(device, cuda_stream)
         self.device = device
         self.set_option(HGRMS_OPT_KERNEL, kernel)
         self.set_option(HGRMS_OPT_PASSES, passes)
+        self.set_option(HGRMS_OPT_AUTOTUNE, int(bool(autotune)))
         self.set_option(HGRMS_OPT_TIMING, int(bool(timing)))
 
     def set_option(self, opt: int, value: int) -> None:

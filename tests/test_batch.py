@@ -199,3 +199,32 @@ def test_fused_relaunches_in_batch(oracle_mod, den, torch_cuda, beta, passes, ma
     outs, ks, conv = run_batch(den, torch_cuda, imgs, 10, beta, max_k, passes=passes, list_cap=list_cap,
                                relaunch_ppm=1)
     check(oracle_mod, imgs, outs, ks, conv, 10, beta, max_k, f"relaunch b={beta} T={passes} cap={list_cap}")
+
+
+def test_autotuner_single_and_batch(oracle_mod, den, torch_cuda):
+    """The autotuner's first call of a class times the candidates without
+    writing the images, then denoises with the fastest; results match the
+    oracle and the second call of the class reuses the choice."""
+    from paper_1306_5390_gb300 import hgrms
+    torch = torch_cuda
+    d = hgrms.Denoiser(0, autotune=True)
+    try:
+        _, noisy = synth.noisy_image(333, 517, 0.35, synth.seed_for(33, 0))
+        ref, k_ref, c_ref = oracle_mod.denoise(noisy, 10, 1, 32)
+        for call in range(2):
+            t = torch.from_numpy(noisy.copy()).cuda()
+            k = d.denoise(t, 10, 1, 32)
+            st = d.stats()
+            assert k == k_ref and d.converged() == bool(c_ref)
+            assert np.array_equal(t.cpu().numpy(), ref)
+            assert st["autotuned"] == 1
+            assert (st["tune_ms"] > 0) == (call == 0)
+            assert hgrms.hgrms_has_kernel(1, st["passes_per_launch"]) == 1
+            assert st["tile_eval_max"] in (1024, 2048, 4096, 8192)
+        imgs = mixed_batch(12, 1000)
+        work = [torch.from_numpy(im.copy()).cuda() for im in imgs]
+        ks = d.denoise_batch(work, 10, 2, 32)
+        assert d.stats()["autotuned"] == 1
+        check(oracle_mod, imgs, [w.cpu().numpy() for w in work], ks, d.converged(), 10, 2, 32, "autotune")
+    finally:
+        d.close()
