@@ -44,7 +44,11 @@ def parse_args(argv=None):
     p.add_argument("--steps", type=int, default=20)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    p.add_argument("--workload", choices=("8192", "256"), default="8192")
+    p.add_argument("--workload", choices=("8192", "256", "serve"), default="8192")
+    p.add_argument("--serve-rate", type=float, default=2000.0, help="serving: requests per second (Poisson)")
+    p.add_argument("--serve-seconds", type=float, default=4.0, help="serving: length of the arrival stream")
+    p.add_argument("--serve-slots", type=int, default=4)
+    p.add_argument("--serve-budget-gb", type=float, default=40.0)
     p.add_argument("--betas", default="1,2,3")
     p.add_argument("--passes", type=int, default=0, help="fused passes per launch (0 = built-in)")
     p.add_argument("--kernel", type=int, default=0,
@@ -420,6 +424,104 @@ def batch_section(torch, local, args):
     }
 
 
+def run_serve(args, rank, world, local):
+    """Serving: a Poisson stream of denoising requests (square images with
+    sides log-uniform in 256..4096, impulse density 5..80 %, alpha 10, beta 1
+    or 2, max_k 32), each on its own device buffer, through the request
+    server (continuous batching under a device-memory budget).  Reports
+    throughput and the latency distribution measured by the server (submit
+    -> result ready)."""
+    import threading
+    import torch
+    from paper_1306_5390_gb300 import build, hgrms, synth
+    build.build()
+    torch.cuda.set_device(local)
+    rng = np.random.Generator(np.random.PCG64(synth.seed_for(4, 0)))
+    pool = []
+    for i in range(48):
+        side = int(round(math.exp(rng.uniform(math.log(256), math.log(4096)))))
+        density = float(rng.uniform(0.05, 0.80))
+        img = synth.noisy_image(side, side, density, synth.seed_for(4, 1 + i))[1]
+        pool.append(torch.from_numpy(img).cuda())
+    n_req = int(args.serve_rate * args.serve_seconds)
+    gaps = rng.exponential(1.0 / args.serve_rate, size=n_req)
+    picks = rng.integers(0, len(pool), size=n_req)
+    betas = rng.integers(1, 3, size=n_req)
+    srv = hgrms.Server(local, hbm_budget_bytes=int(args.serve_budget_gb * (1 << 30)), slots=args.serve_slots)
+    # warm-up: every pool image once per beta (buffers grow to their working size)
+    warm = []
+    for t in pool:
+        for b in (1, 2):
+            x = t.clone()
+            warm.append((x, srv.submit(x, 10, b, 32)))
+    for x, rid in warm:
+        srv.wait(rid)
+    torch.cuda.synchronize()
+    ids = [None] * n_req
+    bufs = [None] * n_req
+    lat, queue_ms, bsz = [], [], []
+    px_iters = [0]
+    done = threading.Event()
+
+    def waiter():
+        for i in range(n_req):
+            while ids[i] is None:
+                time.sleep(0.0002)
+            k, info = srv.wait(ids[i])
+            lat.append(info["latency_ms"])
+            queue_ms.append(info["queue_ms"])
+            bsz.append(info["batch_size"])
+            px_iters[0] += bufs[i].numel() * k
+            bufs[i] = None
+        done.set()
+
+    side = torch.cuda.Stream()
+    th = threading.Thread(target=waiter)
+    th.start()
+    t0 = time.perf_counter()
+    t_next = t0
+    for i in range(n_req):
+        t_next += gaps[i]
+        while time.perf_counter() < t_next:
+            pass
+        with torch.cuda.stream(side):
+            x = pool[int(picks[i])].clone()
+        side.synchronize()
+        bufs[i] = x
+        ids[i] = srv.submit(x, 10, int(betas[i]), 32)
+    t_submitted = time.perf_counter()
+    done.wait()
+    th.join()
+    t_end = time.perf_counter()
+    st = srv.stats()
+    srv.close()
+    wall = t_end - t0
+    lat_a = np.array(lat)
+    out = {
+        "metric": "images/s served (continuous batching, bit-exact per request)",
+        "value": round(n_req / wall, 1), "unit": "images/s", "n_gpus": 1, "steps": n_req, "warmup": 2 * len(pool),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic (seeded Gaussian-bump + gradient content, salt-and-pepper noise)",
+        "config": {"workload": (f"Poisson {args.serve_rate:.0f} req/s for {args.serve_seconds:.1f} s, square images "
+                                "256..4096 (log-uniform, 48 seeded images), salt-and-pepper 5..80%, alpha 10, "
+                                "beta 1 or 2, max_k 32, device-resident"),
+                   "slots": args.serve_slots, "hbm_budget_gb": args.serve_budget_gb},
+        "latency_ms": {"p50": round(float(np.percentile(lat_a, 50)), 3),
+                       "p90": round(float(np.percentile(lat_a, 90)), 3),
+                       "p99": round(float(np.percentile(lat_a, 99)), 3),
+                       "max": round(float(lat_a.max()), 3),
+                       "queue_p50": round(float(np.percentile(queue_ms, 50)), 3)},
+        "offered_rate": args.serve_rate,
+        "achieved_rate": round(n_req / wall, 1),
+        "submit_seconds": round(t_submitted - t0, 3),
+        "mpix_iter_per_s": round(px_iters[0] / wall / 1e6, 1),
+        "batches": st["batches"], "mean_batch": round(float(np.mean(bsz)), 2),
+        "max_in_flight": st["max_in_flight"], "errors": st["error"],
+    }
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+
+
 def traffic_from_profiles(name, beta, T, rows, cols):
     """DRAM bytes per launch of the dominant kernel from a committed ncu
     summary (profiles/<kernel>_b<beta>[_t<T>]_<rows>x<cols>.txt, line
@@ -500,6 +602,8 @@ def main(argv=None):
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "serve":
+        run_serve(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
 

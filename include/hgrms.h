@@ -52,6 +52,7 @@ extern "C" {
 #define HGRMS_ETIMEOUT (-4) /* a bounded device wait gave up */
 #define HGRMS_ENODEV   (-5) /* no CUDA device, or the device index is out of range */
 #define HGRMS_ETOOBIG  (-6) /* image too large for hgrms_denoise_noalloc's fixed scratch */
+#define HGRMS_EAGAIN   (-7) /* hgrms_server_wait: the request is not finished yet */
 
 typedef struct hgrms_ctx* hgrms_t;
 
@@ -131,6 +132,61 @@ int hgrms_last_cuda_error(hgrms_t h);
  * the caller. */
 int hgrms_denoise_noalloc(uint8_t* img, int rows, int cols, int alpha, int beta, int max_k,
                           void* cuda_stream);
+
+/* ---- Serving: continuous batching of requests ------------------------- */
+
+/* A request server on one device.  Requests (one image each, any size, each
+ * with its own alpha, beta and max_k) queue up and are served by `slots`
+ * worker threads, each with its own handle, CUDA stream and an equal share of
+ * `hbm_budget_bytes`.  A slot that becomes free takes, in arrival order,
+ * every queued request with the oldest request's (alpha, beta, max_k) while
+ * their device memory (resident copies of host images plus the batched
+ * schedule's buffers, estimated per pixel) fits its share - the oldest one
+ * always, alone if it exceeds the share - and denoises them with one
+ * hgrms_denoise_batch call; requests that arrive meanwhile join a later
+ * batch, and the batches of different slots run concurrently on the device.
+ * A request's output and k are those of hgrms_denoise on its image alone,
+ * whatever batch it joins (not a method of the paper: a way of running it
+ * for many requests). */
+typedef struct hgrms_server* hgrms_server_t;
+
+typedef struct hgrms_request_info {
+    int    k;           /* the request's k, or its negative error code */
+    double latency_ms;  /* submit -> result ready */
+    double queue_ms;    /* submit -> taken by a slot */
+    int    batch_size;  /* requests in the batch it was served in */
+    int    slot;
+} hgrms_request_info_t;
+
+/* Create a server with `slots` (1..64) workers on `device` and a device
+ * memory budget of hbm_budget_bytes (>= 64 MiB).  Returns HGRMS_OK and the
+ * server in *out, or a negative code. */
+int hgrms_server_create(hgrms_server_t* out, int device, long long hbm_budget_bytes, int slots);
+
+/* Queue one request.  `img` is rows x cols bytes, row-major: device memory of
+ * the server's device (denoised in place; out must be NULL or img) or host
+ * memory (its result is written to `out`, host memory of the same size,
+ * which may be img).  Both must stay valid until hgrms_server_wait returns
+ * for the request.  Writes the request id to *id.  Returns HGRMS_OK or
+ * HGRMS_EINVAL (bad arguments, or the server is shutting down). */
+int hgrms_server_submit(hgrms_server_t s, const uint8_t* img, uint8_t* out, int rows, int cols, int alpha,
+                        int beta, int max_k, unsigned long long* id);
+
+/* Wait for request `id` (at most timeout_s seconds; negative = no limit),
+ * fill *info (if not NULL) and release the request.  Returns its k (>= 0),
+ * its error code, HGRMS_EAGAIN (not finished within the timeout; wait again)
+ * or HGRMS_EINVAL (unknown id, e.g. already waited for). */
+int hgrms_server_wait(hgrms_server_t s, unsigned long long id, double timeout_s, hgrms_request_info_t* info);
+
+/* Counters so far: requests served, batches run, requests queued now, and
+ * the most requests on the device at once.  Returns the first error a batch
+ * met (0 if none). */
+int hgrms_server_stats(hgrms_server_t s, long long* served, long long* batches, long long* queued,
+                       long long* max_in_flight);
+
+/* Serve every queued request, stop the workers and free everything.  NULL is
+ * accepted. */
+void hgrms_server_destroy(hgrms_server_t s);
 
 /* ---- Tuning and measurement (not part of the method) ------------------ */
 

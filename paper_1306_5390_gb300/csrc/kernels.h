@@ -36,3 +36,11 @@ cudaError_t launch_copy_out_batch(const Ctrl* c, uint8_t* const arena[3], const 
 cudaError_t launch_tile_map(const ImgDesc* imgs, int nimg, int total_tiles, int* tile_img, cudaStream_t s);
 
 }  // namespace hg
+
+struct hgrms_ctx;
+namespace hg {
+// Run the handle's list-pass launches on `coop`, a stream shared by handles
+// whose work overlaps (null: the handle's own stream).
+int set_coop_stream(hgrms_ctx* h, cudaStream_t coop);
+
+}  // namespace hg

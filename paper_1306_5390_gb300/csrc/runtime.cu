@@ -77,6 +77,12 @@ struct hgrms_ctx {
     int opt_autotune = 0;
     std::map<long long, Tuning> tuned;  // autotuner choices by (beta, batch, size class)
     cudaEvent_t tune_ev[2] = {nullptr, nullptr};
+    // Stream shared with other handles whose work overlaps this one's (the
+    // request server's slots): the list-pass launch, a cooperative launch
+    // whose CTAs wait for one another, runs there, so two such launches never
+    // share the device.  Null: the handle's own stream.
+    cudaStream_t coop_stream = nullptr;
+    cudaEvent_t coop_ev[2] = {nullptr, nullptr};
 };
 
 namespace hg {
@@ -467,10 +473,17 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
     }
     for (int i = 0; i < launches; ++i) {
         if (timed) HG_TRY(h, cudaEventRecord(h->events[2 * i], s));
-        if (i < fused_launches)
+        if (i < fused_launches) {
             HG_TRY(h, fe->launch(a, (int)tiles_total, s));
-        else
+        } else if (h->coop_stream) {
+            HG_TRY(h, cudaEventRecord(h->coop_ev[0], s));
+            HG_TRY(h, cudaStreamWaitEvent(h->coop_stream, h->coop_ev[0], 0));
+            HG_TRY(h, hg::launch_list(beta, a, h->sms, h->coop_stream));
+            HG_TRY(h, cudaEventRecord(h->coop_ev[1], h->coop_stream));
+            HG_TRY(h, cudaStreamWaitEvent(s, h->coop_ev[1], 0));
+        } else {
             HG_TRY(h, hg::launch_list(beta, a, h->sms, s));
+        }
         if (timed) HG_TRY(h, cudaEventRecord(h->events[2 * i + 1], s));
     }
     if (!write_back) {
@@ -778,6 +791,8 @@ HG_EXPORT void hgrms_destroy(hgrms_t h) {
         for (cudaEvent_t e : h->events) cudaEventDestroy(e);
         for (cudaEvent_t e : h->tune_ev)
             if (e) cudaEventDestroy(e);
+        for (cudaEvent_t e : h->coop_ev)
+            if (e) cudaEventDestroy(e);
     }
     delete h;
 }
@@ -882,6 +897,20 @@ HG_EXPORT int hgrms_denoise_batch(hgrms_t h, uint8_t* const* imgs, const int* ro
     return HGRMS_OK;
 }
 
+namespace hg {
+
+// Run this handle's list-pass launches on `coop` (see hgrms_ctx::coop_stream).
+int set_coop_stream(hgrms_t h, cudaStream_t coop) {
+    if (!h) return HGRMS_EINVAL;
+    DeviceGuard g(h->device);
+    for (int i = 0; i < 2; ++i)
+        if (!h->coop_ev[i]) HG_TRY(h, cudaEventCreateWithFlags(&h->coop_ev[i], cudaEventDisableTiming));
+    h->coop_stream = coop;
+    return HGRMS_OK;
+}
+
+}  // namespace hg
+
 HG_EXPORT int hgrms_converged(hgrms_t h) {
     if (!h) return HGRMS_EINVAL;
     return h->converged;
@@ -896,6 +925,7 @@ HG_EXPORT const char* hgrms_strerror(int code) {
         case HGRMS_ETIMEOUT: return "device wait timed out";
         case HGRMS_ENODEV: return "no CUDA device";
         case HGRMS_ETOOBIG: return "image too large for the fixed scratch of hgrms_denoise_noalloc";
+        case HGRMS_EAGAIN: return "request not finished yet";
         default: return code >= 0 ? "success" : "unknown error";
     }
 }

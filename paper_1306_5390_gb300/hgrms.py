@@ -24,6 +24,7 @@ HGRMS_ECUDA = -3
 HGRMS_ETIMEOUT = -4
 HGRMS_ENODEV = -5
 HGRMS_ETOOBIG = -6
+HGRMS_EAGAIN = -7
 HGRMS_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 HGRMS_OPT_KERNEL = 1
@@ -40,8 +41,19 @@ EXPORTED = (
     "hgrms_create", "hgrms_destroy", "hgrms_denoise", "hgrms_denoise_batch",
     "hgrms_converged", "hgrms_strerror", "hgrms_last_cuda_error", "hgrms_set_option",
     "hgrms_stats", "hgrms_launch_times", "hgrms_default_passes", "hgrms_has_kernel",
-    "hgrms_denoise_noalloc",
+    "hgrms_denoise_noalloc", "hgrms_server_create", "hgrms_server_submit", "hgrms_server_wait",
+    "hgrms_server_stats", "hgrms_server_destroy",
 )
+
+
+class hgrms_request_info_t(ctypes.Structure):
+    _fields_ = [
+        ("k", ctypes.c_int),
+        ("latency_ms", ctypes.c_double),
+        ("queue_ms", ctypes.c_double),
+        ("batch_size", ctypes.c_int),
+        ("slot", ctypes.c_int),
+    ]
 
 
 class hgrms_stats_t(ctypes.Structure):
@@ -117,6 +129,18 @@ def load_library(path: str | None = None):
         lib.hgrms_default_passes.restype = ctypes.c_int
         lib.hgrms_has_kernel.argtypes = [ctypes.c_int, ctypes.c_int]
         lib.hgrms_has_kernel.restype = ctypes.c_int
+        llp = ctypes.POINTER(ctypes.c_longlong)
+        lib.hgrms_server_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.c_longlong, ctypes.c_int]
+        lib.hgrms_server_create.restype = ctypes.c_int
+        lib.hgrms_server_submit.argtypes = [vp, vp, vp] + [ctypes.c_int] * 5 + [ctypes.POINTER(ctypes.c_ulonglong)]
+        lib.hgrms_server_submit.restype = ctypes.c_int
+        lib.hgrms_server_wait.argtypes = [vp, ctypes.c_ulonglong, ctypes.c_double,
+                                          ctypes.POINTER(hgrms_request_info_t)]
+        lib.hgrms_server_wait.restype = ctypes.c_int
+        lib.hgrms_server_stats.argtypes = [vp, llp, llp, llp, llp]
+        lib.hgrms_server_stats.restype = ctypes.c_int
+        lib.hgrms_server_destroy.argtypes = [vp]
+        lib.hgrms_server_destroy.restype = None
         _lib = lib
         return lib
 
@@ -283,3 +307,82 @@ def denoise(img, alpha: int, beta: int, max_k: int, device: int = 0) -> int:
     """One-shot in-place denoise (creates and frees a handle)."""
     with Denoiser(device) as d:
         return d.denoise(img, alpha, beta, max_k)
+
+
+class Server:
+    """Continuous-batching request server (hgrms_server_*): submit images
+    (host numpy arrays, or CUDA tensors denoised in place), wait for results.
+
+        with Server(0, hbm_budget_bytes=40 << 30, slots=4) as srv:
+            rid = srv.submit(img, alpha=10, beta=1, max_k=32)
+            k, info = srv.wait(rid)
+    """
+
+    def __init__(self, device: int = 0, hbm_budget_bytes: int = 40 << 30, slots: int = 4):
+        lib = load_library()
+        h = ctypes.c_void_p()
+        rc = lib.hgrms_server_create(ctypes.byref(h), int(device), int(hbm_budget_bytes), int(slots))
+        if rc != HGRMS_OK:
+            raise HgrmsError(rc, "hgrms_server_create")
+        self.h = h.value
+        self._keep = {}  # request id -> the buffers the request uses
+
+    def submit(self, img, alpha: int, beta: int, max_k: int, out=None) -> int:
+        """Queue `img` (2-D uint8 numpy array or CUDA tensor).  A host image's
+        result goes to `out` (default: in place); returns the request id."""
+        if hasattr(img, "data_ptr"):
+            if not img.is_contiguous():
+                raise ValueError("image must be contiguous")
+            src = img.data_ptr()
+            dst = None
+            rows, cols = img.shape
+        else:
+            if not img.flags["C_CONTIGUOUS"] or img.dtype.itemsize != 1:
+                raise ValueError("image must be a C-contiguous uint8 array")
+            if out is None:
+                out = img
+            src = img.ctypes.data
+            dst = out.ctypes.data
+            rows, cols = img.shape
+        rid = ctypes.c_ulonglong()
+        rc = load_library().hgrms_server_submit(self.h, src, dst, int(rows), int(cols), int(alpha), int(beta),
+                                                int(max_k), ctypes.byref(rid))
+        if rc != HGRMS_OK:
+            raise HgrmsError(rc, "hgrms_server_submit")
+        self._keep[rid.value] = (img, out)
+        return rid.value
+
+    def wait(self, rid: int, timeout_s: float = -1.0):
+        """(k, info dict) of request `rid` once served."""
+        info = hgrms_request_info_t()
+        rc = load_library().hgrms_server_wait(self.h, ctypes.c_ulonglong(rid), float(timeout_s), ctypes.byref(info))
+        if rc == HGRMS_EAGAIN:
+            raise TimeoutError(f"request {rid} not finished")
+        self._keep.pop(rid, None)
+        if rc < 0:
+            raise HgrmsError(rc, "hgrms_server_wait")
+        return rc, {f: getattr(info, f) for f, _ in info._fields_}
+
+    def stats(self) -> dict:
+        v = [ctypes.c_longlong() for _ in range(4)]
+        err = load_library().hgrms_server_stats(self.h, *[ctypes.byref(x) for x in v])
+        return dict(served=v[0].value, batches=v[1].value, queued=v[2].value, max_in_flight=v[3].value,
+                    error=err)
+
+    def close(self) -> None:
+        if self.h:
+            load_library().hgrms_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -96,3 +96,26 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(hgrms, "_lib", None)
     with pytest.raises(RuntimeError, match="not built"):
         hgrms.load_library(str(tmp_path / "nope.so"))
+
+
+def test_server_without_device(lib):
+    """Creating a server needs a CUDA device (ENODEV here); bad arguments
+    are rejected first."""
+    import ctypes
+    from paper_1306_5390_gb300 import hgrms
+    h = ctypes.c_void_p()
+    assert lib.hgrms_server_create(None, 0, 1 << 30, 2) == hgrms.HGRMS_EINVAL
+    assert lib.hgrms_server_create(ctypes.byref(h), 0, 1 << 30, 0) == hgrms.HGRMS_EINVAL
+    rc = lib.hgrms_server_create(ctypes.byref(h), 0, 1 << 30, 2)
+    try:
+        import torch
+        has_gpu = torch.cuda.is_available()
+    except ImportError:
+        has_gpu = False
+    if not has_gpu:
+        assert rc == hgrms.HGRMS_ENODEV and not h.value
+    else:
+        assert rc == hgrms.HGRMS_OK
+        lib.hgrms_server_destroy(h)
+    lib.hgrms_server_destroy(None)  # accepted
+    assert lib.hgrms_server_wait(None, 1, 0.0, None) == hgrms.HGRMS_EINVAL
