@@ -28,8 +28,10 @@
  *     device work and leave the image untouched.
  *   - Images are dense: row r starts at img + r*cols.  No alignment is
  *     required.  The pointer may be device memory of the handle's device
- *     (denoised in place on the device) or host memory (pageable or pinned;
- *     copied to the device and back inside the call).
+ *     (denoised in place on the device), page-locked host memory mapped into
+ *     the device's address space (e.g. from cudaHostAlloc: the device reads
+ *     it and writes the result back to it directly), or other host memory
+ *     (copied to the device and back inside the call).
  *   - Calls are synchronous: when a call returns, the result is in img.
  *     Work is issued on the handle's stream.
  *   - A handle may be used by one host thread at a time.
@@ -76,8 +78,8 @@ int hgrms_denoise(hgrms_t h, uint8_t* img, int rows, int cols,
                   int alpha, int beta, int max_k);
 
 /* Denoise n independent images with the same alpha, beta and max_k, in
- * place.  imgs[i] has rows[i] x cols[i] pixels (all device pointers or all
- * host pointers).  k_out[i] receives image i's k, exactly what
+ * place.  imgs[i] has rows[i] x cols[i] pixels (each device memory or host
+ * memory, as for hgrms_denoise).  k_out[i] receives image i's k, exactly what
  * hgrms_denoise returns for that image alone; image i converged (a further
  * pass would change nothing) exactly when k_out[i] < max_k.  With the
  * default schedule the images are denoised together: one fused launch over

@@ -74,7 +74,7 @@ struct alignas(16) ImgDesc {
     int tiles_x;          // fused-kernel tile grid width
     int tile0;            // first fused-kernel tile of this image
     int bm_words;         // bitmap words per image row
-    uint8_t* user;        // the caller's image (device memory) for the batched copies, or null
+    uint8_t* user;        // the caller's image if the device can read it (batches), or null
 };
 
 // A change-list entry packs (image, row, column) into 32 bits: the column in
@@ -151,6 +151,11 @@ struct PassArgs {
     // pass's changes need at most this many pixel evaluations in the tile
     // (0 = the kernel's built-in value), else as a dense pass.
     int tile_eval_max;
+    // Hybrid schedule: the first fused launch reads a tile of image i from
+    // the caller's image (dense rows of cols bytes; device memory or mapped
+    // page-locked host memory) instead of canvas `cur`: `user0` for a single
+    // image, ImgDesc::user for a batch; null = read the canvas.
+    const uint8_t* user0;
 };
 
 // Passes the launch must run: 0 when the call has finished.

@@ -29,8 +29,6 @@ cudaError_t launch_copy_out(const Ctrl* c, uint8_t* const canvas[3], long long p
 cudaError_t launch_list(int beta, const PassArgs& a, int sms, cudaStream_t s);
 // Batched forms (image table on the device; max_words = the largest image's
 // rows * cols / 4, rounded up, sizes the grid).
-cudaError_t launch_copy_in_batch(const ImgDesc* imgs, int nimg, long long max_words, uint8_t* arena, int sms,
-                                 cudaStream_t s);
 cudaError_t launch_copy_out_batch(const Ctrl* c, uint8_t* const arena[3], const ImgDesc* imgs, int nimg,
                                   long long max_words, int sms, cudaStream_t s);
 cudaError_t launch_tile_map(const ImgDesc* imgs, int nimg, int total_tiles, int* tile_img, cudaStream_t s);

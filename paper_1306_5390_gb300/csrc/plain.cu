@@ -175,34 +175,9 @@ cudaError_t launch_copy_out(const Ctrl* c, uint8_t* const canvas[3], long long p
     return cudaGetLastError();
 }
 
-// Batched copies: grid (per-image CTAs, images); image blockIdx.y, whose
+// Batched copy-out: grid (per-image CTAs, images); image blockIdx.y, whose
 // `user` pointer is the caller's dense image (row r at user + r * cols), or
 // null for an image staged by the host.
-
-// Dense image -> canvas: one aligned 4-byte canvas word per thread; the
-// source bytes come from the aligned words that hold them (only words that
-// hold at least one byte of the image are read; the 1..3 bytes a row's last
-// word takes beyond the image land in the canvas's right padding).
-__global__ void copy_in_batch_kernel(const ImgDesc* __restrict__ imgs, uint8_t* __restrict__ arena) {
-    const ImgDesc d = imgs[blockIdx.y];
-    if (!d.user) return;
-    const uint8_t* src = d.user;
-    uint8_t* canvas = arena + d.off + (long long)kPadY * d.pitch + kPadX;
-    const int nwr = (d.cols + 3) / 4;
-    const long long total = (long long)d.rows * nwr;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long r = i / nwr;
-        const int j = (int)(i - r * nwr);
-        const int n = min(4, d.cols - 4 * j);  // image bytes in this word
-        const uintptr_t ad = reinterpret_cast<uintptr_t>(src + r * d.cols + 4 * j);
-        const uint32_t* q = reinterpret_cast<const uint32_t*>(ad & ~uintptr_t(3));
-        const uint32_t sh = (uint32_t)(ad & 3u);
-        const uint32_t w0 = __ldg(q);
-        const uint32_t w1 = (sh != 0u && (int)sh + n > 4) ? __ldg(q + 1) : 0u;
-        *reinterpret_cast<uint32_t*>(canvas + r * d.pitch + 4 * j) = __funnelshift_r(w0, w1, 8u * sh);
-    }
-}
 
 // Canvas `cur` -> dense image: one aligned 4-byte word of the destination
 // per thread, gathered from the canvas; the partial words at the two ends of
@@ -260,13 +235,6 @@ static unsigned batch_copy_ctas(long long max_words, int nimg, int sms) {
     if (g > lim) g = lim;
     if (g < 1) g = 1;
     return (unsigned)g;
-}
-
-cudaError_t launch_copy_in_batch(const ImgDesc* imgs, int nimg, long long max_words, uint8_t* arena, int sms,
-                                 cudaStream_t s) {
-    if (nimg <= 0) return cudaSuccess;
-    copy_in_batch_kernel<<<dim3(batch_copy_ctas(max_words, nimg, sms), (unsigned)nimg), 256, 0, s>>>(imgs, arena);
-    return cudaGetLastError();
 }
 
 cudaError_t launch_copy_out_batch(const Ctrl* c, uint8_t* const arena[3], const ImgDesc* imgs, int nimg,

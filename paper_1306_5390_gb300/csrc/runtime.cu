@@ -2,7 +2,9 @@
 //
 // One call of hgrms_denoise (or one chunk of hgrms_denoise_batch, whose
 // images are laid out side by side in the same buffers):
-//   1. copy the image(s) into canvas A (padded, 16-byte aligned rows),
+//   1. host images the device cannot read are copied into canvas A (padded,
+//      16-byte aligned rows); the first fused launch reads the others
+//      (device memory, mapped page-locked host memory) directly,
 //   2. reset the device control block (k = 0, current canvas = A),
 //   3. enqueue the passes (Section 2's iteration): by default one fused
 //      launch of T passes on shared-memory tiles of every image (the passes
@@ -159,9 +161,13 @@ int check_args(int rows, int cols, int alpha, int beta, int max_k) {
     return HGRMS_OK;
 }
 
-// Where a pointer lives: 1 = device memory of `device`, 0 = host, -1 = device
-// memory of another device (rejected).
-int pointer_kind(const void* p, int device) {
+// Where a pointer lives: 1 = memory the device reads and writes directly
+// (device memory of `device`, or page-locked host memory mapped into the
+// device's address space, whose device address goes to *devp), 0 = other
+// host memory (staged by copies), -1 = device memory of another device
+// (rejected).
+int pointer_kind(const void* p, int device, uint8_t** devp) {
+    *devp = const_cast<uint8_t*>(static_cast<const uint8_t*>(p));
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
@@ -169,6 +175,10 @@ int pointer_kind(const void* p, int device) {
     }
     if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)
         return at.device == device ? 1 : -1;
+    if (at.type == cudaMemoryTypeHost && at.devicePointer) {
+        *devp = static_cast<uint8_t*>(at.devicePointer);
+        return 1;
+    }
     return 0;
 }
 
@@ -410,18 +420,15 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
         h->table_tiles = (int)tiles_total;
     }
     if (ms) HG_TRY(h, cudaEventRecord(h->tune_ev[0], s));
-    // Images in: device images by kernel, host images by 2-D copies.
-    if (n == 1 && im[0].dev) {
-        HG_TRY(h, hg::launch_copy_in(im[0].ptr, im[0].rows, im[0].cols, h->canvas[0], h->host_desc[0].pitch, h->sms, s));
-    } else {
-        HG_TRY(h, hg::launch_copy_in_batch(h->d_desc, n, max_words, h->canvas[0], h->sms, s));
-        for (int i = 0; i < n; ++i) {
-            if (im[i].dev) continue;
-            const hg::ImgDesc& d = h->host_desc[i];
-            HG_TRY(h, cudaMemcpy2DAsync(h->canvas[0] + d.off + (long long)hg::kPadY * d.pitch + hg::kPadX, (size_t)d.pitch,
-                                        im[i].ptr, (size_t)d.cols, (size_t)d.cols, (size_t)d.rows,
-                                        cudaMemcpyHostToDevice, s));
-        }
+    // Images in: the first fused launch reads the images the device can read
+    // (device memory, mapped page-locked host memory) directly; other host
+    // images are copied into canvas 0, which it reads for them.
+    for (int i = 0; i < n; ++i) {
+        if (im[i].dev) continue;
+        const hg::ImgDesc& d = h->host_desc[i];
+        HG_TRY(h, cudaMemcpy2DAsync(h->canvas[0] + d.off + (long long)hg::kPadY * d.pitch + hg::kPadX, (size_t)d.pitch,
+                                    im[i].ptr, (size_t)d.cols, (size_t)d.cols, (size_t)d.rows,
+                                    cudaMemcpyHostToDevice, s));
     }
     HG_TRY(h, hg::launch_ctrl_init(h->ctrl, (unsigned)max_k, s));
     HG_TRY(h, cudaMemsetAsync(h->bitmaps, 0, 4 * (size_t)bm_total * sizeof(uint32_t), s));
@@ -456,6 +463,7 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
     a.ntiles = (int)tiles_total;
     a.hybrid = 1;
     a.tile_eval_max = tu.eval_max;
+    a.user0 = (n == 1 && im[0].dev) ? im[0].ptr : nullptr;
     const bool user_ppm = h->opt_relaunch_ppm > 0;
     const long long ppm = user_ppm ? h->opt_relaunch_ppm : default_relaunch_ppm(beta);
     a.relaunch_evals = ppm >= 1000000 ? (1ll << 62) : px_total / 1000000 * ppm + px_total % 1000000 * ppm / 1000000;
@@ -486,8 +494,8 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
         }
         if (timed) HG_TRY(h, cudaEventRecord(h->events[2 * i + 1], s));
     }
-    if (!write_back) {
-        // trial: no copy-out
+    if (!write_back || max_k == 0) {
+        // a trial, or no pass ran (the images are unchanged): no copy-out
     } else if (n == 1 && im[0].dev) {
         HG_TRY(h, hg::launch_copy_out(h->ctrl, h->canvas, h->host_desc[0].pitch, im[0].ptr, im[0].rows, im[0].cols,
                                       h->sms, s));
@@ -501,7 +509,7 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
     HG_TRY(h, cudaStreamSynchronize(s));
     const hg::Ctrl c = *h->host_ctrl;
     bool host_out = false;
-    for (int i = 0; i < n && write_back; ++i) {
+    for (int i = 0; i < n && write_back && max_k > 0; ++i) {
         if (im[i].dev) continue;
         const hg::ImgDesc& d = h->host_desc[i];
         HG_TRY(h, cudaMemcpy2DAsync(im[i].ptr, (size_t)d.cols,
@@ -676,6 +684,7 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     a.hybrid = 0;
     a.relaunch_evals = 0;
     a.tile_eval_max = h->opt_tile_eval_max;
+    a.user0 = nullptr;
     // Per-launch timing is limited to calls of at most kMaxTimedLaunches launches.
     constexpr int kMaxTimedLaunches = 4096;
     const bool timed = h->opt_timing && p.launches <= kMaxTimedLaunches;
@@ -802,13 +811,14 @@ HG_EXPORT int hgrms_denoise(hgrms_t h, uint8_t* img, int rows, int cols, int alp
     int rc = check_args(rows, cols, alpha, beta, max_k);
     if (rc < 0) return rc;
     DeviceGuard g(h->device);
-    const int kind = pointer_kind(img, h->device);
+    uint8_t* dp = nullptr;
+    const int kind = pointer_kind(img, h->device, &dp);
     if (kind < 0) return HGRMS_EINVAL;
     h->stats = hgrms_stats_t{};
     h->launch_ms.clear();
     h->launch_kind.clear();
-    if (h->opt_kernel != kHybrid) return denoise_one(h, img, rows, cols, alpha, beta, max_k, kind == 1, true);
-    const BatchImg bi{img, rows, cols, kind == 1};
+    if (h->opt_kernel != kHybrid) return denoise_one(h, dp, rows, cols, alpha, beta, max_k, kind == 1, true);
+    const BatchImg bi{dp, rows, cols, kind == 1};
     int k = 0;
     Tuning tu;
     rc = choose_tuning(h, &bi, 1, alpha, beta, max_k, &k, &tu);
@@ -821,15 +831,15 @@ HG_EXPORT int hgrms_denoise_batch(hgrms_t h, uint8_t* const* imgs, const int* ro
                                   int alpha, int beta, int max_k, int* k_out) {
     if (!h || n < 0 || (n > 0 && (!imgs || !rows || !cols || !k_out))) return HGRMS_EINVAL;
     DeviceGuard g(h->device);
-    int kind0 = -2;
+    std::vector<BatchImg> bi((size_t)n);
     for (int i = 0; i < n; ++i) {
         if (!imgs[i]) return HGRMS_EINVAL;
         int rc = check_args(rows[i], cols[i], alpha, beta, max_k);
         if (rc < 0) return rc;
-        const int kind = pointer_kind(imgs[i], h->device);
+        uint8_t* dp = nullptr;
+        const int kind = pointer_kind(imgs[i], h->device, &dp);
         if (kind < 0) return HGRMS_EINVAL;
-        if (kind0 == -2) kind0 = kind;
-        if (kind != kind0) return HGRMS_EINVAL;
+        bi[i] = BatchImg{dp, rows[i], cols[i], kind == 1};
     }
     h->launch_ms.clear();
     h->launch_kind.clear();
@@ -841,8 +851,6 @@ HG_EXPORT int hgrms_denoise_batch(hgrms_t h, uint8_t* const* imgs, const int* ro
         const hg::FusedEntry* fe = find_fused(beta, T);
         if (!fe) return HGRMS_EINVAL;
         const long long budget = (long long)(h->opt_batch_mb > 0 ? h->opt_batch_mb : 8192) << 20;
-        std::vector<BatchImg> bi((size_t)n);
-        for (int i = 0; i < n; ++i) bi[i] = BatchImg{imgs[i], rows[i], cols[i], kind0 == 1};
         h->stats = hgrms_stats_t{};
         int all_conv = 1;
         for (int start = 0; start < n;) {
@@ -875,7 +883,7 @@ HG_EXPORT int hgrms_denoise_batch(hgrms_t h, uint8_t* const* imgs, const int* ro
     int all_conv = 1;
     for (int i = 0; i < n; ++i) {
         h->stats = hgrms_stats_t{};
-        const int k = denoise_one(h, imgs[i], rows[i], cols[i], alpha, beta, max_k, kind0 == 1, true);
+        const int k = denoise_one(h, bi[i].ptr, rows[i], cols[i], alpha, beta, max_k, bi[i].dev, true);
         if (k < 0) return k;
         k_out[i] = k;
         all_conv &= h->converged;

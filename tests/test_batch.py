@@ -228,3 +228,27 @@ def test_autotuner_single_and_batch(oracle_mod, den, torch_cuda):
         check(oracle_mod, imgs, [w.cpu().numpy() for w in work], ks, d.converged(), 10, 2, 32, "autotune")
     finally:
         d.close()
+
+
+def test_batch_mixing_device_pinned_and_pageable(oracle_mod, den, torch_cuda):
+    """One batch with device images, page-locked host images (read and
+    written by the kernels) and pageable host images (staged by copies)."""
+    torch = torch_cuda
+    imgs = mixed_batch(12, 1100)
+    work, outs_get = [], []
+    for i, im in enumerate(imgs):
+        if i % 3 == 0:
+            t = torch.from_numpy(im.copy()).cuda()
+            work.append(t)
+            outs_get.append(lambda t=t: t.cpu().numpy())
+        elif i % 3 == 1:
+            p = torch.from_numpy(im.copy()).pin_memory()
+            arr = p.numpy()
+            work.append(arr)
+            outs_get.append(lambda arr=arr, p=p: arr.copy())
+        else:
+            arr = im.copy()
+            work.append(arr)
+            outs_get.append(lambda arr=arr: arr.copy())
+    ks = den.denoise_batch(work, 10, 1, 32)
+    check(oracle_mod, imgs, [g() for g in outs_get], ks, den.converged(), 10, 1, 32, "mixed memory")

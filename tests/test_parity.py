@@ -150,6 +150,21 @@ def test_host_pointer_path(oracle_mod, den, torch_cuda):
         assert_same(oracle_mod, den, torch_cuda, noisy, 10, beta, 32, host=True)
 
 
+def test_pinned_host_pointer_path(oracle_mod, den, torch_cuda):
+    """Page-locked host images are read and written by the copy kernels
+    directly (no staging copy); odd shapes and an odd byte offset."""
+    torch = torch_cuda
+    for i, (r, c) in enumerate([(200, 333), (8193 // 8, 1000), (17, 255)]):
+        _, noisy = synth.noisy_image(r, c, 0.3, synth.seed_for(34, i))
+        buf = torch.empty(r * c + 1, dtype=torch.uint8).pin_memory()
+        host = buf.numpy()[1:].reshape(r, c)
+        host[...] = noisy
+        ref, k_ref, c_ref = oracle_mod.denoise(noisy, 10, 1 + i % 2, 32)
+        k = den.denoise(host, 10, 1 + i % 2, 32)
+        assert k == k_ref and den.converged() == bool(c_ref)
+        assert np.array_equal(host, ref), (r, c)
+
+
 def test_unaligned_device_pointer(oracle_mod, den, torch_cuda):
     torch = torch_cuda
     _, noisy = synth.noisy_image(150, 160, 0.3, synth.seed_for(26, 0))
