@@ -404,6 +404,23 @@ def batch_section(torch, local, args):
     ms_b, ks_b = timed(lambda: d.denoise_batch(views, 10, 1, 32), args.batch_steps, 1)
     st = d.stats()
     out_b = work.clone()
+    # The same batch with the learned k-predictor choosing the schedule
+    # (predicted k -> that many passes as fused launches, list passes after).
+    pred = None
+    try:
+        d.load_predictor(1)
+        work.copy_(pristine)
+        k_hat = d.predict_k(1, views)
+        d.set_option(hgrms.HGRMS_OPT_PREDICT_K, 1)
+        ms_p, ks_p = timed(lambda: d.denoise_batch(views, 10, 1, 32), args.batch_steps, 1)
+        same_p = bool(torch.equal(work, out_b)) and list(ks_p) == list(ks_b)
+        d.set_option(hgrms.HGRMS_OPT_PREDICT_K, 0)
+        err = np.abs(k_hat - np.array(ks_b, dtype=np.float32))
+        pred = {"ms_per_step": round(ms_p, 3), "images_per_s": round(n / (ms_p * 1e-3), 1),
+                "k_mae": round(float(err.mean()), 3), "k_abs_err_p90": round(float(np.percentile(err, 90)), 3),
+                "identical_outputs_and_k": same_p, "steps": args.batch_steps}
+    except FileNotFoundError:
+        pred = None
     ms_l, ks_l = timed(lambda: [dl.denoise(v, 10, 1, 32) for v in views], args.loop_steps, 1)
     same = bool(torch.equal(work, out_b)) and list(ks_b) == list(ks_l)
     d.close()
@@ -417,6 +434,7 @@ def batch_section(torch, local, args):
                     "mpix_iter_per_s": round(pix_iters / (ms_b * 1e-3) / 1e6, 1), "steps": args.batch_steps},
         "per_image_loop": {"ms_per_step": round(ms_l, 3), "images_per_s": round(n / (ms_l * 1e-3), 1),
                            "mpix_iter_per_s": round(pix_iters / (ms_l * 1e-3) / 1e6, 1), "steps": args.loop_steps},
+        "batched_predicted_k": pred,
         "speedup": round(ms_l / ms_b, 3),
         "autotuned": {"passes_per_launch": st["passes_per_launch"], "tile_eval_max": st["tile_eval_max"],
                       "tuning_ms": round(tune_ms, 1)},
@@ -446,8 +464,10 @@ def run_serve(args, rank, world, local):
         density = float(rng.uniform(0.05, 0.80))
         img = synth.noisy_image(side, side, density, synth.seed_for(4, 1 + i))[1]
         pool.append(torch.from_numpy(img).cuda())
-    n_req = int(args.serve_rate * args.serve_seconds)
-    gaps = rng.exponential(1.0 / args.serve_rate, size=n_req)
+    # serve_rate 0: no pacing (every request as soon as a buffer is free),
+    # which measures the capacity of the server and this client.
+    n_req = int((args.serve_rate if args.serve_rate > 0 else 20000.0) * args.serve_seconds)
+    gaps = rng.exponential(1.0 / args.serve_rate, size=n_req) if args.serve_rate > 0 else np.zeros(n_req)
     picks = rng.integers(0, len(pool), size=n_req)
     betas = rng.integers(1, 3, size=n_req)
     srv = hgrms.Server(local, hbm_budget_bytes=int(args.serve_budget_gb * (1 << 30)), slots=args.serve_slots)
@@ -460,41 +480,67 @@ def run_serve(args, rank, world, local):
     for x, rid in warm:
         srv.wait(rid)
     torch.cuda.synchronize()
+    # Requests use a ring of device buffers; the waiter thread refills a
+    # buffer with its next request's image (on its own stream) once the
+    # request using it has finished, so submission does no device work.
+    ring = max(64, min(1024, int((args.serve_rate if args.serve_rate > 0 else 20000.0) * 0.05)))
     ids = [None] * n_req
-    bufs = [None] * n_req
+    bufs = [None] * ring
+    ready = [threading.Event() for _ in range(ring)]
     lat, queue_ms, bsz = [], [], []
     px_iters = [0]
     done = threading.Event()
+    refill = torch.cuda.Stream()
+
+    def fill(slot, i):
+        with torch.cuda.stream(refill):
+            src = pool[int(picks[i])]
+            if bufs[slot] is None or bufs[slot].shape != src.shape:
+                bufs[slot] = torch.empty_like(src)
+            bufs[slot].copy_(src)
+        refill.synchronize()
+        ready[slot].set()
+
+    for i in range(min(ring, n_req)):
+        fill(i, i)
 
     def waiter():
         for i in range(n_req):
             while ids[i] is None:
-                time.sleep(0.0002)
+                time.sleep(0.0001)
             k, info = srv.wait(ids[i])
             lat.append(info["latency_ms"])
             queue_ms.append(info["queue_ms"])
             bsz.append(info["batch_size"])
-            px_iters[0] += bufs[i].numel() * k
-            bufs[i] = None
+            px_iters[0] += int(pool[int(picks[i])].numel()) * k
+            if i + ring < n_req:
+                fill(i % ring, i + ring)
         done.set()
 
-    side = torch.cuda.Stream()
+    # The submitting loop sleeps until shortly before each arrival and hands
+    # the interpreter to the waiter thread often.
+    old_switch = sys.getswitchinterval()
+    sys.setswitchinterval(5e-5)
     th = threading.Thread(target=waiter)
     th.start()
     t0 = time.perf_counter()
     t_next = t0
     for i in range(n_req):
-        t_next += gaps[i]
-        while time.perf_counter() < t_next:
-            pass
-        with torch.cuda.stream(side):
-            x = pool[int(picks[i])].clone()
-        side.synchronize()
-        bufs[i] = x
-        ids[i] = srv.submit(x, 10, int(betas[i]), 32)
+        t_next += gaps[i] if args.serve_rate > 0 else 0.0
+        while True:
+            left = t_next - time.perf_counter()
+            if left <= 0:
+                break
+            if left > 3e-4:
+                time.sleep(left - 2e-4)
+        slot = i % ring
+        ready[slot].wait()
+        ready[slot].clear()
+        ids[i] = srv.submit(bufs[slot], 10, int(betas[i]), 32)
     t_submitted = time.perf_counter()
     done.wait()
     th.join()
+    sys.setswitchinterval(old_switch)
     t_end = time.perf_counter()
     st = srv.stats()
     srv.close()
@@ -505,7 +551,8 @@ def run_serve(args, rank, world, local):
         "value": round(n_req / wall, 1), "unit": "images/s", "n_gpus": 1, "steps": n_req, "warmup": 2 * len(pool),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic (seeded Gaussian-bump + gradient content, salt-and-pepper noise)",
-        "config": {"workload": (f"Poisson {args.serve_rate:.0f} req/s for {args.serve_seconds:.1f} s, square images "
+        "config": {"workload": ((f"Poisson {args.serve_rate:.0f} req/s for {args.serve_seconds:.1f} s"
+                                 if args.serve_rate > 0 else f"{n_req} requests without pacing") + ", square images "
                                 "256..4096 (log-uniform, 48 seeded images), salt-and-pepper 5..80%, alpha 10, "
                                 "beta 1 or 2, max_k 32, device-resident"),
                    "slots": args.serve_slots, "hbm_budget_gb": args.serve_budget_gb},

@@ -190,6 +190,36 @@ int hgrms_server_stats(hgrms_server_t s, long long* served, long long* batches, 
  * accepted. */
 void hgrms_server_destroy(hgrms_server_t s);
 
+/* ---- Learned k-predictor (not part of the method) ---------------------- */
+
+/* The paper's concluding section leaves choosing the iteration factor k in
+ * advance as future work.  This predictor estimates k from a 64 x 64
+ * area-averaged copy of the image and a 16-bin histogram of its grey levels
+ * with a 4-layer 3 x 3 convolutional network (16 channels, BF16 operands and
+ * FP32 accumulation on the tensor cores) and a linear head; the estimate
+ * only chooses the schedule (HGRMS_OPT_PREDICT_K).
+ *
+ * Load the network for windows of `beta` (one network per beta; a call with
+ * HGRMS_OPT_PREDICT_K uses the one of its beta, if loaded): weights[n]
+ * holds, in order, conv layer 1 as
+ * [tap 0..8][1][16], layers 2..4 as [tap 0..8][16 inputs][16 outputs]
+ * (tap = 3 (dy + 1) + (dx + 1)), the 4 x 16 biases, then the head: 16
+ * weights on the last layer's channel means, 16 on the histogram and a bias
+ * (n = 144 + 3 * 2304 + 64 + 33 = 7153).  Returns HGRMS_OK, or HGRMS_EINVAL
+ * for a wrong n. */
+int hgrms_predictor_load(hgrms_t h, int beta, const float* weights, int n);
+
+/* Estimate k (windows of `beta`) for n images (device memory or mapped
+ * page-locked host memory,
+ * as for hgrms_denoise; other host memory is rejected with HGRMS_EINVAL):
+ * k_hat[i] >= 0.  Optional outputs (host, NULL to skip): x0 (n x 64 x 64
+ * area means / 255), hist (n x 16 bin fractions; bin = value / 16) and gap
+ * (n x 16 channel means of the last layer).  Returns HGRMS_OK, HGRMS_EINVAL
+ * (no network loaded for beta, bad arguments), HGRMS_ETIMEOUT (a bounded wait for the
+ * tensor cores gave up) or another negative code. */
+int hgrms_predict_k(hgrms_t h, int beta, uint8_t* const* imgs, const int* rows, const int* cols, int n,
+                    float* k_hat, float* x0, float* hist, float* gap);
+
 /* ---- Tuning and measurement (not part of the method) ------------------ */
 
 /* Options for hgrms_set_option. */
@@ -215,6 +245,11 @@ void hgrms_server_destroy(hgrms_server_t s);
                                  passes-per-launch value with switch points 1024..8192 on its own
                                  images, without writing them, and keeps the fastest; the result does
                                  not depend on the choice.  Options 2 and 7, when set, are kept. */
+#define HGRMS_OPT_PREDICT_K 9 /* 1 = before the passes, estimate k with the learned predictor (weights
+                                  from hgrms_predictor_load; device-readable images only) and run
+                                  ceil(k_hat / T) fused launches unconditionally (each stops once a pass
+                                  changes nothing) before the list passes; the results and k do not
+                                  depend on the estimate */
 #define HGRMS_OPT_TILE_EVAL_MAX 7 /* fused kernel: a pass runs as an in-tile list pass while the previous
                                      pass's changes need at most this many evaluations in the tile,
                                      else as a dense pass (0 = built-in: 2048 for beta 2, else
@@ -248,6 +283,8 @@ typedef struct hgrms_stats {
     int    autotuned;       /* 1 if the tuning came from the autotuner (HGRMS_OPT_AUTOTUNE) */
     double tune_ms;         /* device time the autotuner's trials took in this call (0 when the
                                choice was already known) */
+    double k_pred;          /* HGRMS_OPT_PREDICT_K: the largest predicted k of the call's
+                               images, else -1 */
 } hgrms_stats_t;
 
 int hgrms_stats(hgrms_t h, hgrms_stats_t* out);

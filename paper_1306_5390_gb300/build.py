@@ -17,8 +17,8 @@ INCLUDE = os.path.join(os.path.dirname(HERE), "include")
 LIB_DIR = os.path.join(HERE, "_lib")
 OBJ_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(LIB_DIR, "libhgrms.so")
-SOURCES = ["runtime.cu", "plain.cu", "list.cu", "noalloc.cu", "server.cu", "fused_b1.cu", "fused_b2.cu",
-           "fused_b3.cu"]
+SOURCES = ["runtime.cu", "plain.cu", "list.cu", "noalloc.cu", "server.cu", "predictor.cu", "fused_b1.cu",
+           "fused_b2.cu", "fused_b3.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-fvisibility=hidden,-pthread",
               "--expt-relaxed-constexpr"]

@@ -41,4 +41,12 @@ namespace hg {
 // whose work overlaps (null: the handle's own stream).
 int set_coop_stream(hgrms_ctx* h, cudaStream_t coop);
 
+// Learned k-predictor (predictor.cu).
+struct Predictor;
+Predictor* predictor_new();
+void predictor_free(Predictor* p);
+int predictor_load(Predictor* p, const float* weights, int n);
+int predictor_run(Predictor* p, const ImgDesc* imgs, int n, cudaStream_t s, float* k_hat, float* x0_host,
+                  float* hist_host, float* gap_host);
+
 }  // namespace hg

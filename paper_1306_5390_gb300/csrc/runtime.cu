@@ -19,6 +19,7 @@
 #include <stdlib.h>
 #include <string.h>
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <new>
 #include <vector>
@@ -85,6 +86,12 @@ struct hgrms_ctx {
     // share the device.  Null: the handle's own stream.
     cudaStream_t coop_stream = nullptr;
     cudaEvent_t coop_ev[2] = {nullptr, nullptr};
+    // Learned k-predictor (weights loaded by hgrms_predictor_load) and its
+    // image table.
+    hg::Predictor* pred[hg::kMaxBeta + 1] = {};  // by beta
+    hg::ImgDesc* pred_desc = nullptr;
+    int pred_desc_cap = 0;
+    int opt_predict_k = 0;
 };
 
 namespace hg {
@@ -360,7 +367,7 @@ long long hybrid_bytes(const hg::FusedEntry* fe, int rows, int cols) {
 // point.  With write_back false the images are not written (an autotuning
 // trial); *ms, when given, receives the device time of the call's work.
 int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int max_k, int* k_out,
-               const Tuning& tu, bool write_back, float* ms) {
+               const Tuning& tu, bool write_back, float* ms, int forced_fused = 0) {
     const int T = tu.T;
     const hg::FusedEntry* fe = find_fused(beta, T);
     if (!fe) return HGRMS_EINVAL;
@@ -467,7 +474,13 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
     const bool user_ppm = h->opt_relaunch_ppm > 0;
     const long long ppm = user_ppm ? h->opt_relaunch_ppm : default_relaunch_ppm(beta);
     a.relaunch_evals = ppm >= 1000000 ? (1ll << 62) : px_total / 1000000 * ppm + px_total % 1000000 * ppm / 1000000;
-    const int relaunches = ppm >= 1000000 ? 0 : (user_ppm ? kMaxRelaunches : kDefaultRelaunches);
+    int relaunches = ppm >= 1000000 ? 0 : (user_ppm ? kMaxRelaunches : kDefaultRelaunches);
+    if (forced_fused > 0) {
+        // A predicted k: that many passes run as fused launches (each still
+        // stops once a pass changed nothing), the list passes do the rest.
+        a.relaunch_evals = 0;
+        relaunches = std::min(forced_fused - 1, kMaxRelaunches);
+    }
     // Fused launches: the first always runs; each later one runs only while
     // the previous one left many changed pixels (decided on the device).
     // Then one launch runs every remaining pass as a list pass.
@@ -748,6 +761,41 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
 
 }  // namespace
 
+namespace {
+
+// Runs the predictor on the device-readable images of a call; returns the
+// largest estimate (0 when it cannot run: no weights, or an image the
+// device cannot read).
+int predict_max_k(hgrms_ctx* h, const BatchImg* im, int n, int beta, float* out_max) {
+    *out_max = 0.f;
+    if (!h->pred[beta]) return HGRMS_OK;
+    for (int i = 0; i < n; ++i)
+        if (!im[i].dev) return HGRMS_OK;
+    if (n > h->pred_desc_cap) {
+        if (h->pred_desc) cudaFree(h->pred_desc);
+        h->pred_desc = nullptr;
+        h->pred_desc_cap = 0;
+        HG_TRY(h, cudaMalloc(&h->pred_desc, (size_t)n * sizeof(hg::ImgDesc)));
+        h->pred_desc_cap = n;
+    }
+    std::vector<hg::ImgDesc> t((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        memset(&t[i], 0, sizeof(hg::ImgDesc));
+        t[i].rows = im[i].rows;
+        t[i].cols = im[i].cols;
+        t[i].user = im[i].ptr;
+    }
+    HG_TRY(h, cudaMemcpyAsync(h->pred_desc, t.data(), (size_t)n * sizeof(hg::ImgDesc), cudaMemcpyHostToDevice,
+                              h->stream));
+    std::vector<float> kh((size_t)n);
+    const int rc = hg::predictor_run(h->pred[beta], h->pred_desc, n, h->stream, kh.data(), nullptr, nullptr, nullptr);
+    if (rc < 0) return rc;
+    for (float v : kh) *out_max = v > *out_max ? v : *out_max;
+    return HGRMS_OK;
+}
+
+}  // namespace
+
 HG_EXPORT int hgrms_create(hgrms_t* out, int device, void* cuda_stream) {
     if (!out) return HGRMS_EINVAL;
     *out = nullptr;
@@ -802,6 +850,8 @@ HG_EXPORT void hgrms_destroy(hgrms_t h) {
             if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : h->coop_ev)
             if (e) cudaEventDestroy(e);
+        for (hg::Predictor* p : h->pred) hg::predictor_free(p);
+        if (h->pred_desc) cudaFree(h->pred_desc);
     }
     delete h;
 }
@@ -823,7 +873,18 @@ HG_EXPORT int hgrms_denoise(hgrms_t h, uint8_t* img, int rows, int cols, int alp
     Tuning tu;
     rc = choose_tuning(h, &bi, 1, alpha, beta, max_k, &k, &tu);
     if (rc < 0) return rc;
-    rc = run_hybrid(h, &bi, 1, alpha, beta, max_k, &k, tu, true, nullptr);
+    int forced = 0;
+    h->stats.k_pred = -1.0;
+    if (h->opt_predict_k) {
+        float kp = 0.f;
+        rc = predict_max_k(h, &bi, 1, beta, &kp);
+        if (rc < 0) return rc;
+        if (h->pred[beta]) {
+            h->stats.k_pred = kp;
+            forced = (int)std::ceil(std::min(kp, (float)max_k) / (float)tu.T);
+        }
+    }
+    rc = run_hybrid(h, &bi, 1, alpha, beta, max_k, &k, tu, true, nullptr, forced);
     return rc < 0 ? rc : k;
 }
 
@@ -852,6 +913,7 @@ HG_EXPORT int hgrms_denoise_batch(hgrms_t h, uint8_t* const* imgs, const int* ro
         if (!fe) return HGRMS_EINVAL;
         const long long budget = (long long)(h->opt_batch_mb > 0 ? h->opt_batch_mb : 8192) << 20;
         h->stats = hgrms_stats_t{};
+        h->stats.k_pred = -1.0;
         int all_conv = 1;
         for (int start = 0; start < n;) {
             int end = start, mr = 1, mc = 1;
@@ -871,7 +933,18 @@ HG_EXPORT int hgrms_denoise_batch(hgrms_t h, uint8_t* const* imgs, const int* ro
             Tuning tu;
             int rc = choose_tuning(h, bi.data() + start, end - start, alpha, beta, max_k, k_out + start, &tu);
             if (rc < 0) return rc;
-            rc = run_hybrid(h, bi.data() + start, end - start, alpha, beta, max_k, k_out + start, tu, true, nullptr);
+            int forced = 0;
+            if (h->opt_predict_k) {
+                float kp = 0.f;
+                rc = predict_max_k(h, bi.data() + start, end - start, beta, &kp);
+                if (rc < 0) return rc;
+                if (h->pred[beta]) {
+                    h->stats.k_pred = std::max(h->stats.k_pred, (double)kp);
+                    forced = (int)std::ceil(std::min(kp, (float)max_k) / (float)tu.T);
+                }
+            }
+            rc = run_hybrid(h, bi.data() + start, end - start, alpha, beta, max_k, k_out + start, tu, true, nullptr,
+                            forced);
             if (rc < 0) return rc;
             start = end;
         }
@@ -970,6 +1043,10 @@ HG_EXPORT int hgrms_set_option(hgrms_t h, int option, int value) {
             if (value < 0) return HGRMS_EINVAL;
             h->opt_relaunch_ppm = value;
             return HGRMS_OK;
+        case HGRMS_OPT_PREDICT_K:
+            if (value != 0 && value != 1) return HGRMS_EINVAL;
+            h->opt_predict_k = value;
+            return HGRMS_OK;
         case HGRMS_OPT_AUTOTUNE:
             if (value != 0 && value != 1) return HGRMS_EINVAL;
             h->opt_autotune = value;
@@ -1005,4 +1082,41 @@ HG_EXPORT int hgrms_default_passes(int beta) {
 
 HG_EXPORT int hgrms_has_kernel(int beta, int passes) {
     return find_fused(beta, passes) != nullptr ? 1 : 0;
+}
+
+HG_EXPORT int hgrms_predictor_load(hgrms_t h, int beta, const float* weights, int n) {
+    if (!h || !weights || beta < 1 || beta > hg::kMaxBeta) return HGRMS_EINVAL;
+    DeviceGuard g(h->device);
+    if (!h->pred[beta]) h->pred[beta] = hg::predictor_new();
+    if (!h->pred[beta]) return HGRMS_ENOMEM;
+    return hg::predictor_load(h->pred[beta], weights, n);
+}
+
+HG_EXPORT int hgrms_predict_k(hgrms_t h, int beta, uint8_t* const* imgs, const int* rows, const int* cols, int n,
+                              float* k_hat, float* x0, float* hist, float* gap) {
+    if (!h || beta < 1 || beta > hg::kMaxBeta || n < 0 || (n > 0 && (!imgs || !rows || !cols || !k_hat)))
+        return HGRMS_EINVAL;
+    if (!h->pred[beta]) return HGRMS_EINVAL;
+    DeviceGuard g(h->device);
+    std::vector<hg::ImgDesc> t((size_t)n);
+    for (int i = 0; i < n; ++i) {
+        if (!imgs[i] || rows[i] < 1 || cols[i] < 1 || rows[i] > 65536 || cols[i] > 65536) return HGRMS_EINVAL;
+        uint8_t* dp = nullptr;
+        if (pointer_kind(imgs[i], h->device, &dp) != 1) return HGRMS_EINVAL;  // must be device-readable
+        memset(&t[i], 0, sizeof(hg::ImgDesc));
+        t[i].rows = rows[i];
+        t[i].cols = cols[i];
+        t[i].user = dp;
+    }
+    if (n == 0) return HGRMS_OK;
+    if (n > h->pred_desc_cap) {
+        if (h->pred_desc) cudaFree(h->pred_desc);
+        h->pred_desc = nullptr;
+        h->pred_desc_cap = 0;
+        HG_TRY(h, cudaMalloc(&h->pred_desc, (size_t)n * sizeof(hg::ImgDesc)));
+        h->pred_desc_cap = n;
+    }
+    HG_TRY(h, cudaMemcpyAsync(h->pred_desc, t.data(), (size_t)n * sizeof(hg::ImgDesc), cudaMemcpyHostToDevice,
+                              h->stream));
+    return hg::predictor_run(h->pred[beta], h->pred_desc, n, h->stream, k_hat, x0, hist, gap);
 }

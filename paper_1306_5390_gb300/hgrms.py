@@ -35,6 +35,7 @@ HGRMS_OPT_BATCH_MB = 5
 HGRMS_OPT_RELAUNCH_PPM = 6
 HGRMS_OPT_TILE_EVAL_MAX = 7
 HGRMS_OPT_AUTOTUNE = 8
+HGRMS_OPT_PREDICT_K = 9
 
 # Every symbol the header declares (the CPU tests check the library exports them).
 EXPORTED = (
@@ -42,8 +43,10 @@ EXPORTED = (
     "hgrms_converged", "hgrms_strerror", "hgrms_last_cuda_error", "hgrms_set_option",
     "hgrms_stats", "hgrms_launch_times", "hgrms_default_passes", "hgrms_has_kernel",
     "hgrms_denoise_noalloc", "hgrms_server_create", "hgrms_server_submit", "hgrms_server_wait",
-    "hgrms_server_stats", "hgrms_server_destroy",
+    "hgrms_server_stats", "hgrms_server_destroy", "hgrms_predictor_load", "hgrms_predict_k",
 )
+
+PREDICTOR_WEIGHTS = 9 * 16 + 3 * 9 * 16 * 16 + 4 * 16 + 33  # floats per network
 
 
 class hgrms_request_info_t(ctypes.Structure):
@@ -73,6 +76,7 @@ class hgrms_stats_t(ctypes.Structure):
         ("tile_eval_max", ctypes.c_int),
         ("autotuned", ctypes.c_int),
         ("tune_ms", ctypes.c_double),
+        ("k_pred", ctypes.c_double),
     ]
 
     def as_dict(self):
@@ -141,6 +145,11 @@ def load_library(path: str | None = None):
         lib.hgrms_server_stats.restype = ctypes.c_int
         lib.hgrms_server_destroy.argtypes = [vp]
         lib.hgrms_server_destroy.restype = None
+        fp = ctypes.POINTER(ctypes.c_float)
+        lib.hgrms_predictor_load.argtypes = [vp, ctypes.c_int, fp, ctypes.c_int]
+        lib.hgrms_predictor_load.restype = ctypes.c_int
+        lib.hgrms_predict_k.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp), ip, ip, ctypes.c_int, fp, fp, fp, fp]
+        lib.hgrms_predict_k.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -295,6 +304,39 @@ class Denoiser:
 
     def converged(self) -> bool:
         return hgrms_converged(self.h) == 1
+
+    def load_predictor(self, beta: int, weights=None) -> None:
+        """Load the k-predictor network for beta (float32 weights in the
+        order hgrms_predictor_load documents; default: the fitted weights
+        shipped with the package, predictor_b<beta>.npy)."""
+        if weights is None:
+            weights = np.load(os.path.join(os.path.dirname(os.path.abspath(__file__)), f"predictor_b{beta}.npy"))
+        w = np.ascontiguousarray(weights, dtype=np.float32).ravel()
+        rc = load_library().hgrms_predictor_load(self.h, int(beta), w.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                                 int(w.size))
+        if rc != HGRMS_OK:
+            raise HgrmsError(rc, "hgrms_predictor_load")
+
+    def predict_k(self, beta: int, imgs, features: bool = False):
+        """Predicted k per image (device-readable images); with features=True
+        also (x0 [n,64,64], hist [n,16], gap [n,16])."""
+        ps = [self._ptr_shape(im) for im in imgs]
+        n = len(ps)
+        kh = np.zeros(n, dtype=np.float32)
+        fp = ctypes.POINTER(ctypes.c_float)
+        x0 = np.zeros((n, 64, 64), dtype=np.float32) if features else None
+        hist = np.zeros((n, 16), dtype=np.float32) if features else None
+        gap = np.zeros((n, 16), dtype=np.float32) if features else None
+        arr = (ctypes.c_void_p * max(1, n))(*[p[0] for p in ps])
+        rows = (ctypes.c_int * max(1, n))(*[p[1] for p in ps])
+        cols = (ctypes.c_int * max(1, n))(*[p[2] for p in ps])
+
+        def ptr(a):
+            return a.ctypes.data_as(fp) if a is not None else None
+        rc = load_library().hgrms_predict_k(self.h, int(beta), arr, rows, cols, n, ptr(kh), ptr(x0), ptr(hist), ptr(gap))
+        if rc != HGRMS_OK:
+            raise HgrmsError(rc, "hgrms_predict_k")
+        return (kh, x0, hist, gap) if features else kh
 
     def stats(self) -> dict:
         return hgrms_stats(self.h)
