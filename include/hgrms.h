@@ -220,6 +220,25 @@ int hgrms_predictor_load(hgrms_t h, int beta, const float* weights, int n);
 int hgrms_predict_k(hgrms_t h, int beta, uint8_t* const* imgs, const int* rows, const int* cols, int n,
                     float* k_hat, float* x0, float* hist, float* gap);
 
+/* Fit the network on the device (every step on the tensor cores: the
+ * forward convolutions, the gradients of their inputs and of their weights,
+ * then Adam on CUDA cores).  x0 (n x 64 x 64 area means / 255, as
+ * hgrms_predict_k returns them), hist (n x 16) and k (n targets) are host
+ * arrays; weights (host, the order of hgrms_predictor_load) holds the
+ * initial parameters and receives the fitted ones.  Minimises the mean of
+ * (y - k)^2 over minibatches of `batch` images (y: the head before its
+ * ReLU), `epochs` passes over a permutation drawn from `seed` (a 64-bit
+ * linear congruential generator), learning rate lr (lr / 3 in the last
+ * quarter of the epochs).  *loss (if not NULL) receives the last epoch's
+ * mean minibatch loss.  Returns HGRMS_OK or a negative code. */
+int hgrms_predictor_train(hgrms_t h, float* weights, const float* x0, const float* hist, const float* k, int n,
+                          int epochs, int batch, float lr, unsigned long long seed, float* loss);
+
+/* One gradient of that loss over all n images (n <= 4096) for the given
+ * weights: grads (host, the weights' order) and *loss.  For tests. */
+int hgrms_predictor_grad(hgrms_t h, const float* weights, const float* x0, const float* hist, const float* k, int n,
+                         float* grads, float* loss);
+
 /* ---- Tuning and measurement (not part of the method) ------------------ */
 
 /* Options for hgrms_set_option. */

@@ -48,5 +48,9 @@ void predictor_free(Predictor* p);
 int predictor_load(Predictor* p, const float* weights, int n);
 int predictor_run(Predictor* p, const ImgDesc* imgs, int n, cudaStream_t s, float* k_hat, float* x0_host,
                   float* hist_host, float* gap_host);
+int predictor_grad(const float* weights, const float* x0, const float* hist, const float* k, int n, float* grads,
+                   float* loss, cudaStream_t s);
+int predictor_train(float* weights, const float* x0, const float* hist, const float* k, int n, int epochs, int batch,
+                    float lr, unsigned long long seed, float* loss_out, cudaStream_t s);
 
 }  // namespace hg

@@ -1120,3 +1120,17 @@ HG_EXPORT int hgrms_predict_k(hgrms_t h, int beta, uint8_t* const* imgs, const i
                               h->stream));
     return hg::predictor_run(h->pred[beta], h->pred_desc, n, h->stream, k_hat, x0, hist, gap);
 }
+
+HG_EXPORT int hgrms_predictor_grad(hgrms_t h, const float* weights, const float* x0, const float* hist, const float* k,
+                                   int n, float* grads, float* loss) {
+    if (!h || !weights || !x0 || !hist || !k || !grads || !loss) return HGRMS_EINVAL;
+    DeviceGuard g(h->device);
+    return hg::predictor_grad(weights, x0, hist, k, n, grads, loss, h->stream);
+}
+
+HG_EXPORT int hgrms_predictor_train(hgrms_t h, float* weights, const float* x0, const float* hist, const float* k,
+                                    int n, int epochs, int batch, float lr, unsigned long long seed, float* loss) {
+    if (!h || !weights || !x0 || !hist || !k) return HGRMS_EINVAL;
+    DeviceGuard g(h->device);
+    return hg::predictor_train(weights, x0, hist, k, n, epochs, batch, lr, seed, loss, h->stream);
+}

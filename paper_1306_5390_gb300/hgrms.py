@@ -44,6 +44,7 @@ EXPORTED = (
     "hgrms_stats", "hgrms_launch_times", "hgrms_default_passes", "hgrms_has_kernel",
     "hgrms_denoise_noalloc", "hgrms_server_create", "hgrms_server_submit", "hgrms_server_wait",
     "hgrms_server_stats", "hgrms_server_destroy", "hgrms_predictor_load", "hgrms_predict_k",
+    "hgrms_predictor_train", "hgrms_predictor_grad",
 )
 
 PREDICTOR_WEIGHTS = 9 * 16 + 3 * 9 * 16 * 16 + 4 * 16 + 33  # floats per network
@@ -150,6 +151,11 @@ def load_library(path: str | None = None):
         lib.hgrms_predictor_load.restype = ctypes.c_int
         lib.hgrms_predict_k.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp), ip, ip, ctypes.c_int, fp, fp, fp, fp]
         lib.hgrms_predict_k.restype = ctypes.c_int
+        lib.hgrms_predictor_train.argtypes = [vp, fp, fp, fp, fp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_float, ctypes.c_ulonglong, fp]
+        lib.hgrms_predictor_train.restype = ctypes.c_int
+        lib.hgrms_predictor_grad.argtypes = [vp, fp, fp, fp, fp, ctypes.c_int, fp, fp]
+        lib.hgrms_predictor_grad.restype = ctypes.c_int
         _lib = lib
         return lib
 
@@ -316,6 +322,39 @@ class Denoiser:
                                                  int(w.size))
         if rc != HGRMS_OK:
             raise HgrmsError(rc, "hgrms_predictor_load")
+
+    def train_predictor(self, weights, x0, hist, k, epochs: int, batch: int = 256, lr: float = 3e-3,
+                        seed: int = 1):
+        """Fit the predictor on the device; returns (fitted weights, last
+        epoch's mean loss)."""
+        fp = ctypes.POINTER(ctypes.c_float)
+        w = np.ascontiguousarray(weights, dtype=np.float32).ravel().copy()
+        x0 = np.ascontiguousarray(x0, dtype=np.float32)
+        hist = np.ascontiguousarray(hist, dtype=np.float32)
+        k = np.ascontiguousarray(k, dtype=np.float32)
+        loss = ctypes.c_float()
+        rc = load_library().hgrms_predictor_train(self.h, w.ctypes.data_as(fp), x0.ctypes.data_as(fp),
+                                                  hist.ctypes.data_as(fp), k.ctypes.data_as(fp), int(len(k)),
+                                                  int(epochs), int(batch), float(lr), int(seed), ctypes.byref(loss))
+        if rc != HGRMS_OK:
+            raise HgrmsError(rc, "hgrms_predictor_train")
+        return w, loss.value
+
+    def predictor_grad(self, weights, x0, hist, k):
+        """(gradient, loss) of the mean squared k error over all images."""
+        fp = ctypes.POINTER(ctypes.c_float)
+        w = np.ascontiguousarray(weights, dtype=np.float32).ravel()
+        x0 = np.ascontiguousarray(x0, dtype=np.float32)
+        hist = np.ascontiguousarray(hist, dtype=np.float32)
+        k = np.ascontiguousarray(k, dtype=np.float32)
+        g = np.zeros(PREDICTOR_WEIGHTS, dtype=np.float32)
+        loss = ctypes.c_float()
+        rc = load_library().hgrms_predictor_grad(self.h, w.ctypes.data_as(fp), x0.ctypes.data_as(fp),
+                                                 hist.ctypes.data_as(fp), k.ctypes.data_as(fp), int(len(k)),
+                                                 g.ctypes.data_as(fp), ctypes.byref(loss))
+        if rc != HGRMS_OK:
+            raise HgrmsError(rc, "hgrms_predictor_grad")
+        return g, loss.value
 
     def predict_k(self, beta: int, imgs, features: bool = False):
         """Predicted k per image (device-readable images); with features=True

@@ -8,9 +8,10 @@ by the library's exact denoiser (max_k 32; bit-identical to the method's
 definition).  Features (64 x 64 area means, 16-bin histogram) come from the
 library's own feature kernel, so training sees exactly what inference sees.
 The network of hgrms_predictor_load (four 3 x 3 convolutions of 16 channels
-with ReLU, channel means, a linear head on [means, histogram]) is fitted in
-float32 with PyTorch (mean squared error on k, Adam) and written as float32
-in the order hgrms_predictor_load documents.  Prints the mean absolute k
+with ReLU, channel means, a linear head on [means, histogram]) is fitted on
+the device by hgrms_predictor_train (tensor-core forward and backward
+convolutions, mean squared error on k, Adam) and written as float32 in the
+order hgrms_predictor_load documents.  Prints the mean absolute k
 error on held-out images and on the first images of the uneven
 128..2048 workload.
 """
@@ -50,23 +51,6 @@ def labels_and_features(d, beta, imgs, torch, chunk=250):
     return np.array(ks, dtype=np.float32), np.concatenate(x0s), np.concatenate(hists)
 
 
-def export(net, torch) -> np.ndarray:
-    """Float32 weights in hgrms_predictor_load's order."""
-    out = []
-    convs = [m for m in net if isinstance(m, torch.nn.Conv2d)]
-    for conv in convs:
-        w = conv.weight.detach().cpu().numpy()  # [cout][cin][ky][kx]
-        cout, cin = w.shape[:2]
-        t = np.zeros((9, cin, cout), dtype=np.float32)
-        for ky in range(3):
-            for kx in range(3):
-                t[ky * 3 + kx] = w[:, :, ky, kx].T
-        out.append(t.ravel())
-    for conv in convs:
-        out.append(conv.bias.detach().cpu().numpy().astype(np.float32))
-    return np.concatenate(out)
-
-
 def main(argv=None):
     p = argparse.ArgumentParser()
     p.add_argument("--beta", type=int, default=1)
@@ -75,45 +59,27 @@ def main(argv=None):
     p.add_argument("--seed", type=int, default=5)
     p.add_argument("--out", default=os.path.join(HERE, "predictor_b1.npy"))
     args = p.parse_args(argv)
-    import torch
+    import torch  # device memory for the training images
     from paper_1306_5390_gb300 import build, hgrms, synth
     build.build()
-    torch.manual_seed(args.seed)
     d = hgrms.Denoiser(0)
     d.load_predictor(args.beta, np.zeros(hgrms.PREDICTOR_WEIGHTS, dtype=np.float32))
     imgs = list(training_images(args.n, args.seed))
     k, x0, hist = labels_and_features(d, args.beta, imgs, torch)
     n_train = int(0.9 * len(imgs))
-    dev = "cuda"
-    X = torch.from_numpy(x0).unsqueeze(1).to(dev)
-    H = torch.from_numpy(hist).to(dev)
-    Y = torch.from_numpy(k).to(dev)
-    convs = torch.nn.Sequential(
-        torch.nn.Conv2d(1, 16, 3, padding=1), torch.nn.ReLU(),
-        torch.nn.Conv2d(16, 16, 3, padding=1), torch.nn.ReLU(),
-        torch.nn.Conv2d(16, 16, 3, padding=1), torch.nn.ReLU(),
-        torch.nn.Conv2d(16, 16, 3, padding=1), torch.nn.ReLU()).to(dev)
-    head = torch.nn.Linear(32, 1).to(dev)
-    opt = torch.optim.Adam(list(convs.parameters()) + list(head.parameters()), lr=3e-3)
-
-    def forward(xb, hb):
-        g = convs(xb).mean(dim=(2, 3))
-        return head(torch.cat([g, hb], dim=1)).squeeze(1)
-
-    idx = torch.arange(n_train, device=dev)
-    for ep in range(args.epochs):
-        perm = idx[torch.randperm(n_train, device=dev)]
-        for s0 in range(0, n_train, 256):
-            b = perm[s0:s0 + 256]
-            loss = torch.mean((forward(X[b], H[b]) - Y[b]) ** 2)
-            opt.zero_grad()
-            loss.backward()
-            opt.step()
-        if ep == int(args.epochs * 0.75):
-            for gparam in opt.param_groups:
-                gparam["lr"] = 1e-3
-    w = np.concatenate([export(convs, torch), head.weight.detach().cpu().numpy().ravel().astype(np.float32),
-                        head.bias.detach().cpu().numpy().astype(np.float32)])
+    # Initial weights: He-normal convolutions, zero biases, a head that
+    # starts at the mean k.
+    rng = np.random.Generator(np.random.PCG64(args.seed))
+    w0 = np.zeros(hgrms.PREDICTOR_WEIGHTS, dtype=np.float32)
+    off = 0
+    for cin in (1, 16, 16, 16):
+        w0[off:off + 9 * cin * 16] = rng.normal(0.0, np.sqrt(2.0 / (9 * cin)), size=9 * cin * 16)
+        off += 9 * cin * 16
+    w0[-1] = float(k[:n_train].mean())
+    # The fit runs on the device: forward, input and weight gradients of
+    # every convolution on the tensor cores, Adam on CUDA cores.
+    w, loss = d.train_predictor(w0, x0[:n_train], hist[:n_train], k[:n_train], epochs=args.epochs, batch=256,
+                                lr=3e-3, seed=args.seed)
     assert w.size == hgrms.PREDICTOR_WEIGHTS
     np.save(args.out, w)
     # Held-out error, with the library's own (BF16 tensor-core) inference.
@@ -128,7 +94,8 @@ def main(argv=None):
     print(json.dumps({"beta": args.beta, "n": args.n, "held_out": len(held),
                       "held_out_mae": round(float(np.mean(np.abs(kh - k[n_train:]))), 3),
                       "uneven64_mae": round(float(np.mean(np.abs(khu - ku))), 3),
-                      "k_mean_train": round(float(k.mean()), 3), "out": args.out}))
+                      "k_mean_train": round(float(k.mean()), 3), "final_train_loss": round(float(loss), 3),
+                      "out": args.out}))
     d.close()
 
 

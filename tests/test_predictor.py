@@ -146,3 +146,65 @@ def test_predictor_argument_errors(torch_cuda):
         with pytest.raises(hgrms.HgrmsError):
             d.predict_k(2, [np.zeros((8, 8), dtype=np.uint8)])  # pageable host memory
         assert d.predict_k(2, [t]).shape == (1,)
+
+
+def torch_reference_grad(torch, w, x0, hist, k):
+    """Gradient of mean((y - k)^2) in float64 with autograd, from the
+    BF16-rounded weights and inputs the device uses."""
+    nconv = 144 + 3 * 2304  # conv weights are BF16 on the device; biases and head stay FP32
+    wt = torch.tensor(np.concatenate([bf16(w[:nconv]), w[nconv:]]).astype(np.float64), requires_grad=True)
+    x = torch.tensor(bf16(x0).astype(np.float64)).unsqueeze(1)
+    off = 0
+    h = x
+    for l, cin in enumerate((1, 16, 16, 16)):
+        wl = wt[off:off + 9 * cin * 16].view(3, 3, cin, 16).permute(3, 2, 0, 1)  # [co][ci][ky][kx]
+        off += 9 * cin * 16
+        bl = wt[144 + 3 * 2304 + 16 * l: 144 + 3 * 2304 + 16 * (l + 1)]
+        h = torch.relu(torch.nn.functional.conv2d(h, wl, bl, padding=1))
+    head = wt[144 + 3 * 2304 + 64:]
+    g = h.mean(dim=(2, 3))
+    y = head[32] + g @ head[:16] + torch.tensor(hist.astype(np.float64)) @ head[16:32]
+    loss = torch.mean((y - torch.tensor(k.astype(np.float64))) ** 2)
+    loss.backward()
+    return wt.grad.numpy(), float(loss.detach())
+
+
+def test_training_gradient_matches_autograd(torch_cuda):
+    """The device gradient (tensor-core forward, input gradients and weight
+    gradients) against float64 autograd; BF16 activations and gradients on
+    the device bound the agreement to about a percent."""
+    torch = torch_cuda
+    from paper_1306_5390_gb300 import hgrms
+    rng = np.random.Generator(np.random.PCG64(21))
+    n = 12
+    x0 = rng.uniform(0.0, 1.0, size=(n, 64, 64)).astype(np.float32)
+    hist = rng.dirichlet(np.ones(16), size=n).astype(np.float32)
+    k = rng.uniform(0.0, 32.0, size=n).astype(np.float32)
+    w = random_weights(22, scale=0.2)
+    with hgrms.Denoiser(0) as d:
+        g, loss = d.predictor_grad(w, x0, hist, k)
+    g_ref, loss_ref = torch_reference_grad(torch, w, x0, hist, k)
+    assert abs(loss - loss_ref) <= 2e-2 * loss_ref
+    groups = [(0, 144), (144, 2448), (2448, 4752), (4752, 7056), (7056, 7120), (7120, 7153)]
+    for a, b in groups:
+        err = np.linalg.norm(g[a:b] - g_ref[a:b]) / max(np.linalg.norm(g_ref[a:b]), 1e-12)
+        assert err < 5e-2, (a, b, err)
+
+
+def test_training_reduces_loss(torch_cuda):
+    """A learnable target (k grows with the fraction of pixels in the two
+    extreme bins): the device fit cuts the loss several-fold."""
+    torch = torch_cuda
+    from paper_1306_5390_gb300 import hgrms
+    rng = np.random.Generator(np.random.PCG64(23))
+    n = 512
+    x0 = rng.uniform(0.0, 1.0, size=(n, 64, 64)).astype(np.float32)
+    hist = rng.dirichlet(np.ones(16), size=n).astype(np.float32)
+    k = (40.0 * (hist[:, 0] + hist[:, 15]) + 2.0).astype(np.float32)
+    w0 = random_weights(24, scale=0.1)
+    w0[-33:] = 0.0
+    with hgrms.Denoiser(0) as d:
+        _, loss0 = d.predictor_grad(w0, x0, hist, k)
+        w, loss = d.train_predictor(w0, x0, hist, k, epochs=30, batch=64, lr=1e-2, seed=3)
+        _, loss1 = d.predictor_grad(w, x0, hist, k)
+    assert np.isfinite(loss1) and loss1 < 0.2 * loss0, (loss0, loss, loss1)
