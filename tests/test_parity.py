@@ -165,6 +165,23 @@ def test_pinned_host_pointer_path(oracle_mod, den, torch_cuda):
         assert np.array_equal(host, ref), (r, c)
 
 
+@pytest.mark.parametrize("max_k", [9, 10, 13, 20, 31, 32, 40])
+def test_list_pass_endings_device_and_pinned(oracle_mod, den, torch_cuda, max_k):
+    """Runs that end by max_k after a few list passes, by convergence, or
+    after many passes, for device and pinned host images (which the kernels
+    read and write directly), must all give the oracle's bytes and k."""
+    torch = torch_cuda
+    for i, (r, c, dens) in enumerate([(301, 517, 0.3), (200, 200, 0.02), (57, 1000, 0.5)]):
+        _, noisy = synth.noisy_image(r, c, dens, synth.seed_for(35, 10 * i + max_k))
+        assert_same(oracle_mod, den, torch_cuda, noisy, 10, 1, max_k)
+        ref, k_ref, c_ref = oracle_mod.denoise(noisy, 10, 1, max_k)
+        buf = torch.from_numpy(noisy.copy()).pin_memory()
+        host = buf.numpy()
+        den.set_option(1, 0)
+        k = den.denoise(host, 10, 1, max_k)
+        assert k == k_ref and np.array_equal(host, ref), (r, c, max_k)
+
+
 def test_unaligned_device_pointer(oracle_mod, den, torch_cuda):
     torch = torch_cuda
     _, noisy = synth.noisy_image(150, 160, 0.3, synth.seed_for(26, 0))
