@@ -298,6 +298,7 @@ def run_ours(args, rank, world, local):
         "unit": "Gop/s",
         "frac": round(achieved / alu_peak, 4),
         "traffic": traffic_from_profiles(dom_name, dom_b, dom_T, rows, cols),
+        "hbm_achieved_frac": None,
         "algorithmic_unit": (f"one neighbour comparison of Algorithms 1-2 ({(2 * dom_b + 1) ** 2 - 1} per evaluated "
                              "pixel), counting the pixels a pass must evaluate: every pixel in a dense pass, the "
                              "pixels within beta of a previous-pass change otherwise"),
@@ -305,6 +306,9 @@ def run_ours(args, rank, world, local):
         "launch_ms": round(launch_s * 1e3, 4),
         "share_of_step": round(dom_ms / max(1e-9, total_ms), 4),
     }
+    if roofline["traffic"]:
+        # DRAM bytes the kernel moves (ncu) over its measured launch time.
+        roofline["hbm_achieved_frac"] = round(roofline["traffic"] / launch_s / 1e9 / peaks.get("hbm_gbs", 6800.0), 4)
     pix_iters_per_step = units / max(1, args.steps) / world
     step_s = total_ms * 1e-3 / args.steps
     hbm_eff = 2.0 * pix_iters_per_step / step_s / 1e9
@@ -607,6 +611,19 @@ def oracle_sample(w, band_rows, first_row=0):
     return units, time.perf_counter() - t0, band.shape
 
 
+def cpu_model():
+    """Host CPU model name (lscpu or /proc/cpuinfo), or the platform's."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.startswith("Model name:"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def _oracle_band(job):
     w, band_rows, first_row = job
     return oracle_sample(w, band_rows, first_row)
@@ -629,7 +646,9 @@ def cpu_baseline(w, band_rows):
         res = pool.map(_oracle_band, jobs)
     wall = time.perf_counter() - t0
     units = sum(r[0] for r in res)
+    per_core = float(np.mean([r[0] / r[1] for r in res])) / 1e6
     return {"value": round(units / wall / 1e6, 3), "unit": UNIT, "cores": cores, "kind": "oracle",
+            "per_core_value": round(per_core, 3), "cpu_model": cpu_model(),
             "sample": f"{cores} bands of {band_rows} x {w['noisy'].shape[1]} pixels spread over the same image, "
                       f"one spawned process per band (the unmodified C oracle), beta {w['betas']}, "
                       f"max_k {w['max_k']}, {wall:.1f} s wall including process start"}
