@@ -46,20 +46,15 @@ struct Ctrl {
     unsigned long long evals_list;
 };
 
-// Grid barrier of the list-pass loop: CTAs arrive in groups, the last CTA of
-// every group arrives at the root, and the last root arrival releases every
-// group; each counter and each group's release word has its own 128-byte
-// line, so arrivals and polling do not queue behind one hot line.  All zero
-// at the start of a call.
-constexpr int kBarGroups = 16;
+// Grid barrier of the list-pass loop: two 64-bit counters on their own
+// 128-byte lines (barriers alternate between them; see grid_barrier in
+// list.cu).  All zero at the start of a call.
 struct alignas(128) BarLine {
-    unsigned v;
-    unsigned pad[31];
+    unsigned long long v;
+    unsigned long long pad[15];
 };
 struct GridBar {
-    BarLine root;
-    BarLine count[kBarGroups];
-    BarLine gen[kBarGroups];
+    BarLine ctr[2];
 };
 
 // One image of a batch.  The images' canvases are laid out one after another

@@ -66,49 +66,48 @@ __device__ __forceinline__ int eval_pixel(const uint8_t* p, long long stride, in
     return ip;
 }
 
-// Grid-wide barrier over co-resident CTAs (see GridBar) that also ORs one
-// flag over all CTAs.  Arrival counts sit in the low 16 bits of the group and
-// root counters and flag counts in the high bits; the release word of
-// barrier number b is 2b + (OR of the flags).  Every CTA gets the OR through
-// *flag.  The wait is bounded; returns false (for every thread of the CTA)
-// when it gave up.
-__device__ __forceinline__ bool grid_barrier(GridBar* b, Ctrl* c, unsigned nblocks, unsigned& nbar, int* flag) {
+// Grid-wide barrier over co-resident CTAs that also ORs one flag over all
+// CTAs (*flag in, the OR out).  Barrier number b (1, 2, ...) uses
+// counter (b & 1), a 64-bit word whose low half counts arrivals and whose
+// high half counts the arrivals that carried the flag.  Each CTA arrives
+// with one release reduction (no value returned, so no round trip) and polls
+// its counter until the low half reaches the barrier's target; counters are
+// never reset within a call, so the target of the n-th use of a counter is
+// n * nblocks.  The high half's growth since this counter's previous use is
+// the number of flagged arrivals of this barrier: a CTA can arrive at the
+// next barrier of the same counter only after every CTA has passed the
+// barrier in between, hence after every CTA has read this one's value.  The
+// wait is bounded; returns false (for every thread of the CTA) when it gave
+// up.
+__device__ __forceinline__ bool grid_barrier(GridBar* b, Ctrl* c, unsigned nblocks, unsigned& nbar, int* flag,
+                                                  unsigned (&prev_hi)[2]) {
     __shared__ int s_flag;
     const int mine = __syncthreads_or(*flag);
     int ok = 1;
     if (threadIdx.x == 0) {
         const unsigned bn = nbar + 1u;
-        const unsigned ng = nblocks < (unsigned)kBarGroups ? nblocks : (unsigned)kBarGroups;
-        const unsigned grp = blockIdx.x % ng;
-        const unsigned gsize = (nblocks - grp + ng - 1u) / ng;
+        const unsigned par = bn & 1u;
+        unsigned long long* ctr = &b->ctr[par].v;
+        const unsigned long long add = 1ull + (mine ? (1ull << 32) : 0ull);
+        const unsigned target = ((bn + 1u) >> 1) * nblocks;  // uses of this counter so far x CTAs
         __threadfence();
-        const unsigned og = atomicAdd(&b->count[grp].v, 1u + (mine ? 0x10000u : 0u));
-        if ((og & 0xffffu) == gsize - 1u) {
-            const unsigned gflag = ((og >> 16) + (mine ? 1u : 0u)) ? 1u : 0u;
-            b->count[grp].v = 0u;
-            __threadfence();
-            const unsigned orr = atomicAdd(&b->root.v, 1u + (gflag << 16));
-            if ((orr & 0xffffu) == ng - 1u) {
-                const unsigned all = ((orr >> 16) + gflag) ? 1u : 0u;
-                b->root.v = 0u;
-                __threadfence();  // orders every release below after all prior writes
-                for (unsigned j = 0; j < ng; ++j) *reinterpret_cast<volatile unsigned*>(&b->gen[j].v) = 2u * bn + all;
-            }
-        }
-        unsigned spins = 0, word = 0;
+        asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(ctr), "l"(add) : "memory");
+        unsigned spins = 0;
+        unsigned long long v = 0;
         while (true) {
-            word = *reinterpret_cast<volatile const unsigned*>(&b->gen[grp].v);
-            if ((word >> 1) == bn) break;
+            asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
+            if ((unsigned)v >= target) break;
             if (++spins > (1u << 22)) {  // one to two seconds
                 atomicExch(&c->error, 1u);
                 ok = 0;
                 break;
             }
-            if (spins > 64) __nanosleep(32);
+            if (spins > 16) __nanosleep(64);
         }
-        __threadfence();  // later reads see every write released by the barrier
+        const unsigned hi = (unsigned)(v >> 32);
+        s_flag = ok ? (hi != prev_hi[par] ? 1 : 0) : 0;
+        prev_hi[par] = hi;
         nbar = bn;
-        s_flag = ok ? (int)(word & 1u) : 0;
     }
     ok = __syncthreads_and(ok);
     *flag = s_flag;
@@ -173,6 +172,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
     __syncthreads();
     if (s_np == 0) return;  // the fused launch already finished the call
     unsigned k = s_k, cur = s_cur, aux = s_aux, gen = s_gen;
+    unsigned prev_hi[2] = {0u, 0u};  // thread 0: flag counts seen at the last use of each barrier counter
     const int base = (int)s_base;
     const unsigned max_k = s_maxk;
     bool converged = false, failed = false;
@@ -363,7 +363,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
         }
         ++passes;
         int changed = any ? 1 : 0;
-        if (!grid_barrier(a.bar, ctrl, gridDim.x, gen, &changed)) {
+        if (!grid_barrier(a.bar, ctrl, gridDim.x, gen, &changed, prev_hi)) {
             failed = true;
             break;
         }
