@@ -201,6 +201,7 @@ struct StagedList {
     static constexpr int kCap = 256;  // entries per warp buffer
     uint32_t* buf;                    // this warp's buffer
     int n;                            // entries in it (warp-uniform)
+    unsigned total;                   // entries this warp appended since it was last reset (warp-uniform)
 };
 
 // Warp-collective: append this lane's value when `want`.  A buffer that
@@ -222,6 +223,7 @@ __device__ __forceinline__ void staged_append(StagedList& sl, uint32_t* list, un
     }
     if (want) sl.buf[sl.n + __popc(bal & ((1u << lane) - 1u))] = v;
     sl.n += __popc(bal);
+    sl.total += (unsigned)__popc(bal);
 }
 
 // Block-collective (all threads): write every warp's staged entries to the

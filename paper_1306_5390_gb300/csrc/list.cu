@@ -66,29 +66,29 @@ __device__ __forceinline__ int eval_pixel(const uint8_t* p, long long stride, in
     return ip;
 }
 
-// Grid-wide barrier over co-resident CTAs that also ORs one flag over all
-// CTAs (*flag in, the OR out).  Barrier number b (1, 2, ...) uses
-// counter (b & 1), a 64-bit word whose low half counts arrivals and whose
-// high half counts the arrivals that carried the flag.  Each CTA arrives
-// with one release reduction (no value returned, so no round trip) and polls
-// its counter until the low half reaches the barrier's target; counters are
-// never reset within a call, so the target of the n-th use of a counter is
-// n * nblocks.  The high half's growth since this counter's previous use is
-// the number of flagged arrivals of this barrier: a CTA can arrive at the
+// Grid-wide barrier over co-resident CTAs that also sums one count over all
+// CTAs (*count: this CTA's contribution, in shared memory; *total receives
+// the sum).  Barrier number b (1, 2, ...) uses counter (b & 1), a 64-bit
+// word whose low half counts arrivals and whose high half accumulates the
+// counts.  Each CTA arrives with one release reduction (no value returned,
+// so no round trip) and polls its counter until the low half reaches the
+// barrier's target; counters are never reset within a call, so the target
+// of the n-th use of a counter is n * nblocks.  The high half's growth since
+// this counter's previous use is this barrier's sum: a CTA can arrive at the
 // next barrier of the same counter only after every CTA has passed the
 // barrier in between, hence after every CTA has read this one's value.  The
 // wait is bounded; returns false (for every thread of the CTA) when it gave
 // up.
-__device__ __forceinline__ bool grid_barrier(GridBar* b, Ctrl* c, unsigned nblocks, unsigned& nbar, int* flag,
-                                                  unsigned (&prev_hi)[2]) {
-    __shared__ int s_flag;
-    const int mine = __syncthreads_or(*flag);
+__device__ __forceinline__ bool grid_barrier(GridBar* b, Ctrl* c, unsigned nblocks, unsigned& nbar,
+                                             const unsigned* count, unsigned (&prev_hi)[2], unsigned& total) {
+    __shared__ unsigned s_total;
+    __syncthreads();
     int ok = 1;
     if (threadIdx.x == 0) {
         const unsigned bn = nbar + 1u;
         const unsigned par = bn & 1u;
         unsigned long long* ctr = &b->ctr[par].v;
-        const unsigned long long add = 1ull + (mine ? (1ull << 32) : 0ull);
+        const unsigned long long add = 1ull + ((unsigned long long)*count << 32);
         const unsigned target = ((bn + 1u) >> 1) * nblocks;  // uses of this counter so far x CTAs
         __threadfence();
         asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(ctr), "l"(add) : "memory");
@@ -105,12 +105,12 @@ __device__ __forceinline__ bool grid_barrier(GridBar* b, Ctrl* c, unsigned nbloc
             if (spins > 16) __nanosleep(64);
         }
         const unsigned hi = (unsigned)(v >> 32);
-        s_flag = ok ? (hi != prev_hi[par] ? 1 : 0) : 0;
+        s_total = ok ? hi - prev_hi[par] : 0u;
         prev_hi[par] = hi;
         nbar = bn;
     }
     ok = __syncthreads_and(ok);
-    *flag = s_flag;
+    total = s_total;
     return ok != 0;
 }
 
@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
     constexpr int kWarps = kListThreads / 32;
     __shared__ int s_np;
     __shared__ unsigned s_k, s_cur, s_aux, s_maxk, s_gen, s_base;
-    __shared__ unsigned s_n, s_nclr;
+    __shared__ unsigned s_n, s_nclr, s_app;
     __shared__ uint32_t stage_all[kWarps][StagedList::kCap];
     __shared__ int s_counts[kWarps + 1];
     __shared__ unsigned long long s_evals;
@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
     __syncthreads();
     if (s_np == 0) return;  // the fused launch already finished the call
     unsigned k = s_k, cur = s_cur, aux = s_aux, gen = s_gen;
-    unsigned prev_hi[2] = {0u, 0u};  // thread 0: flag counts seen at the last use of each barrier counter
+    unsigned prev_hi[2] = {0u, 0u};  // thread 0: counts seen at the last use of each barrier counter
     const int base = (int)s_base;
     const unsigned max_k = s_maxk;
     bool converged = false, failed = false;
@@ -196,7 +196,17 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
     }
     constexpr int kXb = 16, kYb = 16;
     const int xb = kBatch ? a.xb : kXb, yb = kBatch ? a.yb : kYb;
-    StagedList sl{stage_all[warp], 0};
+    StagedList sl{stage_all[warp], 0, 0u};
+    // List lengths: n_cur = entries of the list this pass reads (appended by
+    // the previous pass), n_last = those of the list the previous pass read
+    // (whose bitmap this pass clears); later lengths come from the barrier.
+    if (tid == 0) {
+        s_n = __ldcg(&ctrl->list_n[base]);
+        s_nclr = __ldcg(&ctrl->list_n[(base + 3) & 3]);
+        s_app = 0u;
+    }
+    __syncthreads();
+    unsigned n_cur = s_n, n_last = s_nclr;
 
     for (int t = 0; k < max_k; ++t) {
         const int si = (t + base) & 3, so = (t + base + 1) & 3, sc = (t + base + 3) & 3;
@@ -207,17 +217,12 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
         uint32_t* next = a.lists[so];
         uint32_t* bm_next = a.bitmaps[so];
         unsigned* nnext = &ctrl->list_n[so];
-        if (tid == 0) {
-            s_n = __ldcg(&ctrl->list_n[si]);
-            s_nclr = __ldcg(&ctrl->list_n[sc]);
-            if (blockIdx.x == 0) {
-                // Set (t + base + 2) % 4 is next written by pass t + 1; its
-                // list was last read (to clear its bitmap) in pass t - 1.
-                ctrl->list_n[(t + base + 2) & 3] = 0u;
-            }
+        if (tid == 0 && blockIdx.x == 0) {
+            // Set (t + base + 2) % 4 is next written by pass t + 1; its list
+            // was last read (to clear its bitmap) in pass t - 1.
+            ctrl->list_n[(t + base + 2) & 3] = 0u;
         }
-        __syncthreads();
-        const unsigned n = s_n, nclr = s_nclr;
+        const unsigned n = n_cur, nclr = n_last;
         // Clear bitmap sc (written by pass t - 2, read by pass t - 1) for pass
         // t + 2: walk its list, or clear it all if the list overflowed.
         {
@@ -235,7 +240,6 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
                 for (long long i = gtid; i < a.bm_total; i += gthreads) bm_clr[i] = 0u;
             }
         }
-        bool any = false;
         if (n <= a.list_cap) {
             // One thread per (changed pixel p, window offset) pair; q = p +
             // offset is evaluated by the thread of its owner.
@@ -309,7 +313,6 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
                         }
                     }
                 }
-                any |= ch;
                 if (kBatch && a.img_k) mark_image(s_imgbits, ch, img, lane);
                 staged_append(sl, next, nnext, a.list_cap, ch, v, lane);
                 pk = pk_next;
@@ -341,8 +344,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
                             atomicOr(bm_next + d.bm_off + (size_t)y * d.bm_words + (x >> 5), 1u << (x & 31));
                         }
                     }
-                    any |= ch;
-                    if (kBatch && a.img_k) mark_image(s_imgbits, ch, (unsigned)im, lane);
+                        if (kBatch && a.img_k) mark_image(s_imgbits, ch, (unsigned)im, lane);
                     staged_append(sl, next, nnext, a.list_cap, ch, v, lane);
                 }
             }
@@ -362,12 +364,18 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
             }
         }
         ++passes;
-        int changed = any ? 1 : 0;
-        if (!grid_barrier(a.bar, ctrl, gridDim.x, gen, &changed, prev_hi)) {
+        // Entries this CTA appended (every changed pixel appends one).
+        if (lane == 0 && sl.total) atomicAdd(&s_app, sl.total);
+        sl.total = 0u;
+        unsigned appended = 0;
+        if (!grid_barrier(a.bar, ctrl, gridDim.x, gen, &s_app, prev_hi, appended)) {
             failed = true;
             break;
         }
-        if (!changed) {
+        if (tid == 0) s_app = 0u;  // read by thread 0 inside the barrier only
+        n_last = n_cur;
+        n_cur = appended;
+        if (appended == 0u) {
             converged = true;  // a fixed point: the output canvas equals the input
             break;
         }
