@@ -269,6 +269,8 @@ int hgrms_predictor_grad(hgrms_t h, const float* weights, const float* x0, const
                                   ceil(k_hat / T) fused launches unconditionally (each stops once a pass
                                   changes nothing) before the list passes; the results and k do not
                                   depend on the estimate */
+#define HGRMS_OPT_LIST_CTAS 10 /* CTAs of the list-pass launch (0 = built-in: one per SM below
+                                   16 M pixels, else as many as can be co-resident, 2 per SM) */
 #define HGRMS_OPT_TILE_EVAL_MAX 7 /* fused kernel: a pass runs as an in-tile list pass while the previous
                                      pass's changes need at most this many evaluations in the tile,
                                      else as a dense pass (0 = built-in: 2048 for beta 2, else

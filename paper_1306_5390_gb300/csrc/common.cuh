@@ -151,6 +151,7 @@ struct PassArgs {
     // page-locked host memory) instead of canvas `cur`: `user0` for a single
     // image, ImgDesc::user for a batch; null = read the canvas.
     const uint8_t* user0;
+    int list_ctas;            // list-pass loop CTAs (0 = as many as can be co-resident)
 };
 
 // Passes the launch must run: 0 when the call has finished.

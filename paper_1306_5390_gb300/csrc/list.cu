@@ -411,7 +411,8 @@ cudaError_t launch_loop_b(const PassArgs& a, int sms, cudaStream_t s) {
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, list_loop_kernel<B, kBatch>, kListThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const unsigned grid = (unsigned)(sms * (per_sm < 2 ? per_sm : 2));
+    unsigned grid = (unsigned)(sms * (per_sm < 2 ? per_sm : 2));
+    if (a.list_ctas > 0 && (unsigned)a.list_ctas < grid) grid = (unsigned)a.list_ctas;
     PassArgs arg = a;
     void* params[] = {&arg};
     return cudaLaunchCooperativeKernel((const void*)list_loop_kernel<B, kBatch>, dim3(grid), dim3(kListThreads),

@@ -127,6 +127,7 @@ extern "C" __attribute__((visibility("default"))) int hgrms_denoise_noalloc(uint
     a.relaunch_evals = 0;
     a.tile_eval_max = 0;
     a.user0 = nullptr;
+    a.list_ctas = 0;
 
     // The array keeps the previous call's contents: the control block is
     // reset by ctrl_init and change map 0 (written by the first launch) is

@@ -36,6 +36,7 @@ HGRMS_OPT_RELAUNCH_PPM = 6
 HGRMS_OPT_TILE_EVAL_MAX = 7
 HGRMS_OPT_AUTOTUNE = 8
 HGRMS_OPT_PREDICT_K = 9
+HGRMS_OPT_LIST_CTAS = 10
 
 # Every symbol the header declares (the CPU tests check the library exports them).
 EXPORTED = (
