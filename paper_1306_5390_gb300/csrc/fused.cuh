@@ -34,11 +34,23 @@
 // fp16 (exact for 0..255), two pixels per 32-bit word.  For a centre value
 // c and neighbour v, closed <=> -alpha < v - c <= alpha <=> |v - (c + 0.5)|
 // < alpha.  With e = v - (c + 0.5) (a half-integer, exact in fp16) the value
-// sat(2 alpha - 2|e|) is exactly 1 when closed and exactly 0 otherwise (the
-// argument is an odd integer), so one subtract, one fused multiply-add with
-// saturation and one add count two pixels' neighbours.  A count of 0 or 1 is
-// an fp16 bit pattern with bit 14 clear; 2 and above have it set.
+// sat(2 alpha - 2|e|) is exactly 1 when closed and exactly +0 otherwise (the
+// argument is an odd integer), so one subtract and one fused multiply-add
+// with saturation test two pixels against one neighbour each.
 //
+// Counting on the integer pipe (beta <= 3).  The two fp16 instructions above
+// run on the FMA pipe; the 0/1 results are summed as 32-bit integers instead
+// of with a third fp16 add (bit patterns 0x0000 / 0x3C00 per half, two
+// results per three-input add), which moves a third of the per-neighbour
+// work to the ALU pipe.  After K_lo and K_hi closed neighbours (K <= 48 for
+// beta <= 3; wider windows keep an fp16 running count) the low half holds 15360 K_lo mod 2^16 and
+// the high half 15360 K_hi + c (mod 2^16), c = floor(15360 K_lo / 2^16) <= 11
+// being the carry out of the low half.  Since 15360 = 1024 * 15 and 47 * 15 =
+// 1 (mod 64), multiplying the word by 47 leaves 1024 (K_lo mod 64) in the
+// low half and 1024 (K_hi mod 64) + r, r < 1024, in the high half, so byte 1
+// of the product is 4 K_lo and byte 3 is 4 K_hi + (0..2): "at most one
+// closed neighbour" is "byte & 0xF8 == 0" for both.
+
 // Work layout: a pass computes rows [R0, R0 + 64) and columns [8, 264).  In
 // a dense pass warp w walks rows [R0 + 8w, R0 + 8w + 8) with a register ring
 // of the 2 beta + 1 window rows, lane l owning the 8 pixels at columns
@@ -155,10 +167,23 @@ __device__ __forceinline__ void load_row_shfl(const uint32_t* __restrict__ rowp,
     make_pairs<B>(w, r);
 }
 
+// Running closed-neighbour count of a segment's 8 pixels.  For beta <= 3
+// (at most 48 neighbours, so K mod 64 is K) acc[j] sums the 0/1 results of
+// pixels 2j, 2j + 1 as integers (see the header), two results per add, the
+// first of each pair waiting in pend.  Wider windows keep the count in fp16
+// (exact up to 2048): h[j] = h[j] + result.
+template <int B>
+struct Count {
+    static constexpr bool kInt = (2 * B + 1) * (2 * B + 1) - 1 < 64;
+    uint32_t acc[4];
+    uint32_t pend[4];
+    int n;  // results so far (a compile-time constant after unrolling)
+};
+
 // Add row `dy`'s closed neighbours to the counts of the segment's 8 pixels.
 template <int B>
 __device__ __forceinline__ void count_row(const Row<B>& rr, const int dy, const __half2 (&cp)[4],
-                                          const __half2 two_a, __half2 (&cnt)[4]) {
+                                          const __half2 two_a, Count<B>& c) {
     const __half2 m2 = __float2half2_rn(-2.f);
 #pragma unroll
     for (int dx = -B; dx <= B; ++dx) {
@@ -167,29 +192,50 @@ __device__ __forceinline__ void count_row(const Row<B>& rr, const int dy, const 
         for (int j = 0; j < 4; ++j) {
             const __half2 e = __hsub2(u2h(rr.p[2 * j + dx + B]), cp[j]);
             const __half2 f = __hfma2_sat(__habs2(e), m2, two_a);
-            cnt[j] = __hadd2(cnt[j], f);
+            if constexpr (Count<B>::kInt) {
+                if (c.n & 1)
+                    c.acc[j] += c.pend[j] + h2u(f);
+                else
+                    c.pend[j] = h2u(f);
+            } else {
+                c.acc[j] = h2u(__hadd2(u2h(c.acc[j]), f));
+            }
         }
+        ++c.n;
     }
 }
 
 template <int B>
-__device__ __forceinline__ void centre_setup(const Row<B>& c, __half2 (&cp)[4], __half2 (&cnt)[4], uint4& centre) {
+__device__ __forceinline__ void centre_setup(const Row<B>& c, __half2 (&cp)[4], Count<B>& cnt, uint4& centre) {
     const __half2 half_ = __float2half2_rn(0.5f);
     centre = make_uint4(c.p[B], c.p[B + 2], c.p[B + 4], c.p[B + 6]);
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
         cp[j] = __hadd2(u2h(c.p[2 * j + B]), half_);
-        cnt[j] = __float2half2_rn(0.f);
+        cnt.acc[j] = 0u;  // also fp16 +0
+    }
+    cnt.n = 0;
+}
+
+// Bit 7 of each byte: the pixel has two or more closed neighbours.  Bytes
+// are pixels 4i .. 4i + 3 for the pair (acc[2i], acc[2i + 1]).  Integer
+// counts: each byte is 4 K (+ 0..2), see the header.  fp16 counts: the high
+// byte of a count of 0 or 1 has bit 6 clear, of 2 and above set.
+template <int B>
+__device__ __forceinline__ uint32_t not_candidate_bits(const uint32_t acc_a, const uint32_t acc_b) {
+    if constexpr (Count<B>::kInt) {
+        const uint32_t q = __byte_perm(acc_a * 47u, acc_b * 47u, 0x7531);
+        return (((q & 0x78787878u) + 0x7F7F7F7Fu) | q) & 0x80808080u;  // byte & 0xF8 != 0
+    } else {
+        return (__byte_perm(acc_a, acc_b, 0x7531) << 1) & 0x80808080u;
     }
 }
 
-// 8-bit mask of the segment's pixels with at most one closed neighbour
-// (count bit 14 clear).
-__device__ __forceinline__ uint32_t candidate_mask(const __half2 (&cnt)[4]) {
-    const uint32_t a = __byte_perm(h2u(cnt[0]), h2u(cnt[1]), 0x7531);  // high bytes
-    const uint32_t b = __byte_perm(h2u(cnt[2]), h2u(cnt[3]), 0x7531);
-    const uint32_t ma = ((~a >> 6) & 0x01010101u) * 0x01020408u >> 24;  // pixel i -> bit i
-    const uint32_t mb = ((~b >> 6) & 0x01010101u) * 0x01020408u >> 24;
+// 8-bit mask (pixel i -> bit i) of the pixels with at most one closed
+// neighbour, from the two words of not_candidate_bits.
+__device__ __forceinline__ uint32_t candidate_mask(const uint32_t na, const uint32_t nb) {
+    const uint32_t ma = ((~na >> 7) & 0x01010101u) * 0x01020408u >> 24;
+    const uint32_t mb = ((~nb >> 7) & 0x01010101u) * 0x01020408u >> 24;
     return (ma & 0xFu) | ((mb & 0xFu) << 4);
 }
 
@@ -361,7 +407,8 @@ __device__ __forceinline__ void band_dense(PassCtx<B, T>& c, const int ys, const
 #pragma unroll
     for (int r = 0; r < G::kRows; ++r) {
         const int y = ys + r;
-        __half2 cp[4], cnt[4];
+        __half2 cp[4];
+        Count<B> cnt;
         uint4 centre;
         if constexpr (kRing) {
 #pragma unroll
@@ -383,9 +430,9 @@ __device__ __forceinline__ void band_dense(PassCtx<B, T>& c, const int ys, const
             }
         }
         *reinterpret_cast<uint4*>(c.out + y * G::SWW + ws) = centre;
-        const uint32_t all = h2u(cnt[0]) & h2u(cnt[1]) & h2u(cnt[2]) & h2u(cnt[3]);
-        if ((all & 0x40004000u) != 0x40004000u)
-            m64 |= (unsigned long long)candidate_mask(cnt) << (8 * r);
+        const uint32_t na = not_candidate_bits<B>(cnt.acc[0], cnt.acc[1]);
+        const uint32_t nb = not_candidate_bits<B>(cnt.acc[2], cnt.acc[3]);
+        if ((na & nb) != 0x80808080u) m64 |= (unsigned long long)candidate_mask(na, nb) << (8 * r);
     }
     constexpr int kHalf = G::kRows / 2;  // rows per append (a half band fits the list)
     constexpr unsigned long long kHalfMask = (1ull << (8 * kHalf)) - 1ull;
