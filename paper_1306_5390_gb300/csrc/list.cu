@@ -4,10 +4,15 @@
 // A pixel's output in pass t depends only on its (2 beta + 1)^2 window in the
 // image of pass t-1, so a pixel with no changed pixel (in pass t-1) within
 // beta keeps its value.  Each pass walks the list of pixels the previous
-// pass changed; one thread takes one (changed pixel p, window offset) pair
-// and evaluates q = p + offset if p "owns" q: p is the first changed pixel,
-// in raster order, of q's window (read from the previous pass's change
-// bitmap), so each pixel is evaluated exactly once.  Results go to the
+// pass changed and evaluates every pixel q within beta of one of them once,
+// by the changed pixel p that "owns" q: the first changed pixel, in raster
+// order, of q's window (read from the previous pass's change bitmap).  For
+// beta 1 one thread takes one (changed pixel, window offset) pair and
+// evaluates q if p owns it.  For wider windows one thread takes one (changed
+// pixel, window row) pair, decides ownership for the whole row from one
+// bitmap word per window row, and queues the owned pixels in shared memory;
+// the CTA then evaluates its queue with all threads, so the evaluations run
+// without idle lanes.  Results go to the
 // partner canvas, which already agrees with the current image at every pixel
 // that is not evaluated (see Ctrl); pixels that change form the next list and
 // bitmap.  When the previous list overflowed its capacity, the pass evaluates
@@ -154,10 +159,14 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
     __shared__ int s_counts[kWarps + 1];
     __shared__ unsigned long long s_evals;
     __shared__ uint32_t s_imgbits[kBatch ? kMaxBatchImages / 32 : 1];  // images changed in this pass (by this CTA)
+    __shared__ uint32_t s_queue[B == 1 ? 1 : kListThreads * W];  // pixels this CTA evaluates in the current chunk
+    __shared__ int s_qn[2];  // queue lengths; chunks alternate between them
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     Ctrl* ctrl = a.ctrl;
     if (tid == 0) {
         s_evals = 0ull;
+        s_qn[0] = 0;
+        s_qn[1] = 0;
         s_np = launch_passes(ctrl, 1);
         s_k = __ldcg(&ctrl->k);
         s_cur = __ldcg(&ctrl->cur);
@@ -178,6 +187,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
     bool converged = false, failed = false;
     int passes = 0;
     unsigned evals = 0;
+    int qpar = 0;  // queue counter of the next chunk (CTA-uniform)
     const long long gthreads = (long long)gridDim.x * blockDim.x;
     const long long gtid = (long long)blockIdx.x * blockDim.x + tid;
     const long long warp_base = (long long)blockIdx.x * blockDim.x + (tid & ~31);
@@ -240,9 +250,10 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
                 for (long long i = gtid; i < a.bm_total; i += gthreads) bm_clr[i] = 0u;
             }
         }
-        if (n <= a.list_cap) {
-            // One thread per (changed pixel p, window offset) pair; q = p +
-            // offset is evaluated by the thread of its owner.
+        if (n <= a.list_cap && B == 1) {
+            // beta 1 (nine window offsets): one thread per (changed pixel p,
+            // window offset) pair, which measured faster there than the
+            // two-phase form below.
             const long long total = (long long)n * P;
             // The list entry of the next iteration is loaded one iteration early.
             long long i = warp_base + lane;
@@ -315,6 +326,128 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
                 }
                 if (kBatch && a.img_k) mark_image(s_imgbits, ch, img, lane);
                 staged_append(sl, next, nnext, a.list_cap, ch, v, lane);
+                pk = pk_next;
+            }
+        } else if (n <= a.list_cap) {
+            // Chunks of one task per thread: task (changed pixel p, window
+            // row dy) finds the pixels q = p + (dy, dx) that p owns and
+            // queues them in shared memory (phase A); the CTA then evaluates
+            // its queue with every thread (phase B).  Tasks are dealt to the
+            // CTAs in turn (task c0 + tid * gridDim.x + blockIdx.x of chunk
+            // c0), so every CTA gets an equal share even when there are fewer
+            // tasks than threads.
+            const long long ntask = (long long)n * W;
+            long long i = (long long)tid * gridDim.x + blockIdx.x;
+            uint32_t pk = i < ntask ? __ldcg(prev + (unsigned)(i / W)) : 0u;  // loaded one chunk early
+            for (long long c0 = 0; c0 + blockIdx.x < ntask; c0 += gthreads, i += gthreads) {
+                const long long inext = i + gthreads;
+                const uint32_t pk_next = inext < ntask ? __ldcg(prev + (unsigned)(inext / W)) : 0u;
+                // Phase A.  Ownership: no changed pixel of q's window precedes
+                // p in raster order.  rb[r] = the previous pass's changes in
+                // row qy - B + r, columns px - 2B .. px + 2B (bit j: column
+                // px - 2B + j); q = (qy, px + dx) has window columns bits
+                // dx + B .. dx + 3B, its rows above py must have none and row
+                // py none left of p (bits below 2B).
+                unsigned own = 0u;  // bit dx + B: this task evaluates q
+                unsigned img = 0;
+                int py = 0, px = 0, qy = 0;
+                if (i < ntask) {
+                    const int dy = (int)(i % W) - B;
+                    unpack_entry(pk, xb, yb, img, py, px);
+                    const ImgDesc d = kBatch ? load_desc(a.imgs, img) : one;
+                    qy = py + dy;
+                    if (qy >= B && qy < d.rows - B) {
+                        const uint32_t* bmp = bm_prev + d.bm_off;
+                        uint32_t rb[2 * B + 1];
+#pragma unroll
+                        for (int r = 0; r <= 2 * B; ++r) {
+                            const int gy = qy - B + r;
+                            rb[r] = (gy <= py) ? row_bits(bmp + (size_t)gy * d.bm_words, d.bm_words, px - 2 * B) : 0u;
+                        }
+                        uint32_t before = 0u;
+#pragma unroll
+                        for (int r = 0; r <= 2 * B; ++r) {
+                            const int gy = qy - B + r;
+                            if (gy < py) before |= rb[r];
+                            if (gy == py) before |= rb[r] & ((1u << (2 * B)) - 1u);
+                        }
+#pragma unroll
+                        for (int dx = -B; dx <= B; ++dx) {
+                            const int qx = px + dx;
+                            const uint32_t wm = ((1u << W) - 1u) << (dx + B);
+                            if (qx >= B && qx < d.cols - B && (before & wm) == 0u) own |= 1u << (dx + B);
+                        }
+                    }
+                }
+                {
+                    // Queue the owned pixels (one shared atomic per warp).
+                    const int cnt = __popc(own);
+                    int incl = cnt;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const int v = __shfl_up_sync(0xffffffffu, incl, o);
+                        if (lane >= o) incl += v;
+                    }
+                    const int wtot = __shfl_sync(0xffffffffu, incl, 31);
+                    int wbase = 0;
+                    if (lane == 31 && wtot) wbase = atomicAdd(&s_qn[qpar], wtot);
+                    int pos = __shfl_sync(0xffffffffu, wbase, 31) + incl - cnt;
+                    while (own) {
+                        const int b = __ffs(own) - 1;
+                        own &= own - 1u;
+                        s_queue[pos++] = pack_entry(img, qy, px + b - B, xb, yb);
+                    }
+                }
+                __syncthreads();
+                // Phase B: Algorithm 2 for every queued pixel.
+                const int qn = s_qn[qpar];
+                // The other counter was last read before the previous chunk's
+                // final barrier and is next used after this chunk's.
+                if (tid == 0) s_qn[qpar ^ 1] = 0;
+                for (int j0 = warp * 32; j0 < qn; j0 += kListThreads) {
+                    const int j = j0 + lane;
+                    bool ch = false;
+                    uint32_t v = 0;
+                    unsigned qimg = 0;
+                    if (j < qn) {
+                        int y, x;
+                        unpack_entry(s_queue[j], xb, yb, qimg, y, x);
+                        const ImgDesc d = kBatch ? load_desc(a.imgs, qimg) : one;
+                        const uint8_t* in = in_arena + d.off + (long long)kPadY * d.pitch + kPadX;
+                        constexpr int NW = (W + 3) / 4;
+                        uint32_t win[W][NW];
+                        const long long off = (long long)y * d.pitch + x;
+#pragma unroll
+                        for (int r = 0; r < W; ++r) load_row_bytes<W>(in + off + (long long)(r - B) * d.pitch - B, win[r]);
+                        ++evals;
+                        const int ip = (int)((win[B][B / 4] >> (8 * (B % 4))) & 0xffu);
+                        int sum = 0, flag = 0;
+#pragma unroll
+                        for (int r = 0; r < W; ++r)
+#pragma unroll
+                            for (int jj = 0; jj < W; ++jj) {
+                                const int tv = (int)((win[r][jj / 4] >> (8 * (jj % 4))) & 0xffu);
+                                const bool open = !(tv < ip + a.alpha + 1 && tv > ip - a.alpha);
+                                sum += open ? tv * tv : 0;
+                                flag += open ? 1 : 0;
+                            }
+                        int nv = ip;
+                        if (flag > P - 3) {
+                            const float qf = floorf(__fdiv_rn((float)sum, (float)flag));
+                            nv = (int)floorf(__fsqrt_rn(qf));
+                        }
+                        out_arena[d.off + (long long)kPadY * d.pitch + kPadX + off] = (uint8_t)nv;
+                        if (nv != ip) {
+                            ch = true;
+                            v = pack_entry(qimg, y, x, xb, yb);
+                            atomicOr(bm_next + d.bm_off + (size_t)y * d.bm_words + (x >> 5), 1u << (x & 31));
+                        }
+                    }
+                    if (kBatch && a.img_k) mark_image(s_imgbits, ch, qimg, lane);
+                    staged_append(sl, next, nnext, a.list_cap, ch, v, lane);
+                }
+                __syncthreads();  // every thread has read the queue
+                qpar ^= 1;
                 pk = pk_next;
             }
         } else {
