@@ -84,6 +84,11 @@ struct FusedGeo {
     static constexpr int CN = 256;                   // computed columns
     static constexpr int P = (2 * B + 1) * (2 * B + 1);
     static constexpr int kCandCap = kRows / 2 * 256;  // per-warp candidate list (half a band)
+    // beta 3: dense passes count in two stages (band_dense2; for beta 2 the
+    // single-stage count measured faster); the second half of a warp's
+    // candidate buffer then holds its stage-two work list.
+    static constexpr bool kTwoStage = B == 3 && kRows == 8;
+    static constexpr int kCandLimit = kTwoStage ? kCandCap / 2 : kCandCap;
     static constexpr int kListCap = 2048;            // changed pixels kept per pass
     static constexpr int kListEvalMax = 2048;        // default: list-pass evaluations above which a pass runs dense
     static constexpr int kMarkWords = (SH * SW + 31) / 32;
@@ -381,7 +386,7 @@ __device__ __forceinline__ void append_bits(PassCtx<B, T>& c, const int lane, ui
     if (!__any_sync(0xffffffffu, m != 0u)) return;
     int total;
     const int off0 = warp_excl_scan(lane, __popc(m), &total);
-    if (c.ncand + total > G::kCandCap) flush_candidates<B, T>(c, lane);
+    if (c.ncand + total > G::kCandLimit) flush_candidates<B, T>(c, lane);
     int off = c.ncand + off0;
     while (m) {
         const int b = __ffs(m) - 1;
@@ -438,6 +443,137 @@ __device__ __forceinline__ void band_dense(PassCtx<B, T>& c, const int ys, const
     constexpr unsigned long long kHalfMask = (1ull << (8 * kHalf)) - 1ull;
     append_bits<B, T>(c, lane, (uint32_t)(m64 & kHalfMask), ys, 2 * ws);
     append_bits<B, T>(c, lane, (uint32_t)((m64 >> (8 * kHalf)) & kHalfMask), ys + kHalf, 2 * ws);
+}
+
+// Outer-ring closed-neighbour count of one pixel pair (the fp16 pair at
+// word xw of tile row y): the window positions with |dy| >= 2 or |dx| >= 2,
+// summed as integers (see the header; 40 results for beta 3).
+template <int B, int SWW>
+__device__ __forceinline__ uint32_t outer_count(const uint32_t* __restrict__ in, const int y, const int xw,
+                                                const __half2 cp, const __half2 two_a) {
+    constexpr int WB = (B + 1) / 2;  // words needed beyond each side of the pair
+    const __half2 m2 = __float2half2_rn(-2.f);
+    uint32_t acc = 0u, pend = 0u;
+    int n = 0;
+#pragma unroll
+    for (int dy = -B; dy <= B; ++dy) {
+        const uint32_t* row = in + (y + dy) * SWW + xw;
+        uint32_t w[2 * WB + 1];
+#pragma unroll
+        for (int k = 0; k <= 2 * WB; ++k) w[k] = row[k - WB];
+#pragma unroll
+        for (int dx = -B; dx <= B; ++dx) {
+            if (dy >= -1 && dy <= 1 && dx >= -1 && dx <= 1) continue;
+            // fp16 pair of the pixels at offsets dx, dx + 1 from the pair's first pixel
+            const uint32_t pw = (dx & 1) ? __byte_perm(w[WB + (dx - 1) / 2], w[WB + (dx + 1) / 2], 0x5432)
+                                         : w[WB + dx / 2];
+            const __half2 e = __hsub2(u2h(pw), cp);
+            const uint32_t f = h2u(__hfma2_sat(__habs2(e), m2, two_a));
+            if (n & 1)
+                acc += pend + f;
+            else
+                pend = f;
+            ++n;
+        }
+    }
+    return acc;
+}
+
+// Dense pass over the warp's 8-row band in two stages (beta 3).  Stage one
+// counts every pixel's closed neighbours in the inner 3 x 3 ring, packed as
+// in band_dense; a pixel with two or more already has too many to be a
+// candidate.  The other pixels' pairs go to a per-warp work list (row,
+// lane, pair and the pixels' stage-one state: not settled, one closed
+// neighbour) and stage two counts only the outer ring for them, one pair per
+// lane.  Pixels with at most one closed neighbour in all are candidates.
+template <int B, int T>
+__device__ __forceinline__ void band_dense2(PassCtx<B, T>& c, const int ys, const int ws, const int lane,
+                                            const __half2 two_a) {
+    using G = FusedGeo<B, T>;
+    constexpr int kHalf = G::kRows / 2;
+    uint16_t* items = c.cand + G::kCandCap / 2;
+    Row<1> win[3];
+    load_row_shfl<1>(c.in + (ys - 1) * G::SWW + ws, win[1]);
+    load_row_shfl<1>(c.in + ys * G::SWW + ws, win[2]);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        // Stage one.  U: pixels not settled (8 bits per row), K: those of
+        // them with one closed neighbour in the inner ring.
+        uint32_t U = 0u, K = 0u;
+#pragma unroll
+        for (int rr = 0; rr < kHalf; ++rr) {
+            const int y = ys + h * kHalf + rr;
+            win[0] = win[1];
+            win[1] = win[2];
+            load_row_shfl<1>(c.in + (y + 1) * G::SWW + ws, win[2]);
+            __half2 cp[4];
+            Count<1> cnt;
+            uint4 centre;
+            centre_setup<1>(win[1], cp, cnt, centre);
+#pragma unroll
+            for (int dy = -1; dy <= 1; ++dy) count_row<1>(win[dy + 1], dy, cp, two_a, cnt);
+            *reinterpret_cast<uint4*>(c.out + y * G::SWW + ws) = centre;
+            // Bytes 4 K (+ 0..2) of the four pixels of each word (see the header).
+            const uint32_t qa = __byte_perm(cnt.acc[0] * 47u, cnt.acc[1] * 47u, 0x7531);
+            const uint32_t qb = __byte_perm(cnt.acc[2] * 47u, cnt.acc[3] * 47u, 0x7531);
+            const uint32_t na = (((qa & 0x78787878u) + 0x7F7F7F7Fu) | qa) & 0x80808080u;  // K >= 2
+            const uint32_t nb = (((qb & 0x78787878u) + 0x7F7F7F7Fu) | qb) & 0x80808080u;
+            const uint32_t u8 = candidate_mask(na, nb);
+            const uint32_t ka = ((qa >> 2) & 0x01010101u) * 0x01020408u >> 24;
+            const uint32_t kb = ((qb >> 2) & 0x01010101u) * 0x01020408u >> 24;
+            const uint32_t k8 = ((ka & 0xFu) | ((kb & 0xFu) << 4)) & u8;
+            U |= u8 << (8 * rr);
+            K |= k8 << (8 * rr);
+        }
+        // Work list: pair j of row rr when one of its pixels is not settled.
+        uint32_t im = 0u;
+#pragma unroll
+        for (int rr = 0; rr < kHalf; ++rr)
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if ((U >> (8 * rr + 2 * j)) & 3u) im |= 1u << (4 * rr + j);
+        if (!__any_sync(0xffffffffu, im != 0u)) continue;
+        int total;
+        int pos = warp_excl_scan(lane, __popc(im), &total);
+        while (im) {
+            const int b = __ffs(im) - 1;
+            im &= im - 1u;
+            const int rr = b >> 2, j = b & 3;
+            const uint32_t fl = ((U >> (8 * rr + 2 * j)) & 3u) | (((K >> (8 * rr + 2 * j)) & 3u) << 2);
+            items[pos++] = (uint16_t)((h * kHalf + rr) | (lane << 3) | (j << 8) | (fl << 10));
+        }
+        __syncwarp();
+        // Stage two.
+        for (int base = 0; base < total; base += 32) {
+            const int i = base + lane;
+            uint32_t cb = 0u;  // bit h: pixel 2 xw + h is a candidate
+            int q0 = 0;
+            if (i < total) {
+                const uint32_t e = items[i];
+                const int y = ys + (int)(e & 7u);
+                const int xw = ws - 4 * lane + 4 * (int)((e >> 3) & 31u) + (int)((e >> 8) & 3u);
+                const uint32_t fl = e >> 10;
+                const __half2 cpair = __hadd2(u2h(c.in[y * G::SWW + xw]), __float2half2_rn(0.5f));
+                const uint32_t z = outer_count<B, G::SWW>(c.in, y, xw, cpair, two_a) * 47u;
+                const uint32_t blo = (z >> 8) & 0xFFu, bhi = z >> 24;  // 4 K_outer (+ 0..2)
+                // At most one closed neighbour in all: K_outer <= 1 - K_inner.
+                if ((fl & 1u) && blo < (((fl >> 2) & 1u) ? 4u : 8u)) cb |= 1u;
+                if ((fl & 2u) && bhi < (((fl >> 3) & 1u) ? 4u : 8u)) cb |= 2u;
+                q0 = y * G::SW + 2 * xw;
+            }
+            // Append the candidates (one shared counter update per warp).
+            if (__any_sync(0xffffffffu, cb != 0u)) {
+                int tot2;
+                const int off = warp_excl_scan(lane, __popc(cb), &tot2);
+                if (c.ncand + tot2 > G::kCandLimit) flush_candidates<B, T>(c, lane);
+                int o = c.ncand + off;
+                if (cb & 1u) c.cand[o++] = (uint16_t)q0;
+                if (cb & 2u) c.cand[o++] = (uint16_t)(q0 + 1);
+                c.ncand += tot2;
+            }
+        }
+        __syncwarp();
+    }
 }
 
 // List pass: only pixels within beta of a pixel that changed in the
@@ -681,7 +817,10 @@ fused_kernel(PassArgs a) {
             const bool dense = (t == 0 && !from_map) || nprev > G::kListCap || nprev * G::P > eval_max;
             if (dense) {
                 ++dense_passes;
-                band_dense<B, T>(c, ys, ws, lane, two_a);
+                if constexpr (G::kTwoStage)
+                    band_dense2<B, T>(c, ys, ws, lane, two_a);
+                else
+                    band_dense<B, T>(c, ys, ws, lane, two_a);
                 flush_candidates<B, T>(c, lane);
             } else {
                 list_pass<B, T>(c, prev, nprev, marks + (t & 1) * G::kMarkWords, tid);
