@@ -32,7 +32,8 @@
  *     the device's address space (e.g. from cudaHostAlloc: the device reads
  *     it and writes the result back to it directly), or other host memory
  *     (copied to the device and back inside the call).
- *   - Calls are synchronous: when a call returns, the result is in img.
+ *   - Calls are synchronous: when a call returns, the result is in img
+ *     (hgrms_denoise_async is the exception: hgrms_wait completes it).
  *     Work is issued on the handle's stream.
  *   - A handle may be used by one host thread at a time.
  *   - Limits: 1 <= rows, cols <= 65536; 0 <= alpha <= 255; 1 <= beta <= 7;
@@ -55,6 +56,7 @@ extern "C" {
 #define HGRMS_ENODEV   (-5) /* no CUDA device, or the device index is out of range */
 #define HGRMS_ETOOBIG  (-6) /* image too large for hgrms_denoise_noalloc's fixed scratch */
 #define HGRMS_EAGAIN   (-7) /* hgrms_server_wait: the request is not finished yet */
+#define HGRMS_EBUSY    (-8) /* the handle has an asynchronous call that hgrms_wait has not finished */
 
 typedef struct hgrms_ctx* hgrms_t;
 
@@ -91,6 +93,30 @@ int hgrms_denoise(hgrms_t h, uint8_t* img, int rows, int cols,
 int hgrms_denoise_batch(hgrms_t h, uint8_t* const* imgs, const int* rows,
                         const int* cols, int n, int alpha, int beta, int max_k,
                         int* k_out);
+
+/* Queue the denoising of one image on the handle's stream and return at once
+ * (HGRMS_OK or a negative code); hgrms_wait finishes the call and returns k.
+ * Same method, arguments, limits and result as hgrms_denoise (Sections 2-3:
+ * the passes of Algorithms 1-2 repeated until a pass changes nothing or k =
+ * max_k), but `img` must be memory the device reads directly: device memory
+ * of the handle's device, or page-locked host memory mapped into its address
+ * space (other host memory: HGRMS_EINVAL).  The result is in img once the
+ * handle's stream has reached the end of the call (hgrms_wait, or any later
+ * work on that stream).  Several handles created on the same stream can each
+ * have one call queued, so consecutive calls run back to back on the device
+ * with no host round trip between them; the handles' list-pass launches then
+ * never overlap.  A handle admits one outstanding call: until hgrms_wait, its
+ * other denoising calls return HGRMS_EBUSY.  Options that need the host
+ * between launches (HGRMS_OPT_AUTOTUNE, HGRMS_OPT_PREDICT_K, HGRMS_OPT_KERNEL
+ * other than 0) make the call run to completion before it returns. */
+int hgrms_denoise_async(hgrms_t h, uint8_t* img, int rows, int cols,
+                        int alpha, int beta, int max_k);
+
+/* Wait for the call queued by hgrms_denoise_async and return its k (or the
+ * negative code of its failure); the statistics, launch times and
+ * hgrms_converged then describe it.  HGRMS_EINVAL when no call is
+ * outstanding. */
+int hgrms_wait(hgrms_t h);
 
 /* 1 if the last hgrms_denoise ended because a pass changed no pixel (the
  * image is a fixed point), 0 if it stopped at max_k, negative on a bad

@@ -93,6 +93,16 @@ struct hgrms_ctx {
     hg::ImgDesc* pred_desc = nullptr;
     int pred_desc_cap = 0;
     int opt_predict_k = 0;
+    // The call that hgrms_denoise_async queued and hgrms_wait has not yet
+    // finished (see PendingCall).
+    struct PendingCall {
+        bool active = false;  // a call is outstanding
+        bool done = false;    // it already ran synchronously; `result` holds its return value
+        int result = 0;
+        int n = 0, max_k = 0, launches = 0, fused_launches = 0, T = 0, eval_max = 0, TH = 0, TW = 0;
+        long long tiles_total = 0;
+        bool per_image_k = false, write_back = false, timed = false;
+    } pending;
 };
 
 namespace hg {
@@ -367,8 +377,15 @@ long long hybrid_bytes(const hg::FusedEntry* fe, int rows, int cols) {
 // `tu` gives the fused passes per launch and the in-tile list/dense switch
 // point.  With write_back false the images are not written (an autotuning
 // trial); *ms, when given, receives the device time of the call's work.
+int finish_hybrid(hgrms_ctx* h, const hgrms_ctx::PendingCall& pd, const BatchImg* im, int* k_out, float* ms);
+
+// Queue one hybrid call (or one chunk of a batch) on the handle's stream.
+// Synchronous calls then wait for it and finish (finish_hybrid); with
+// `async_call` the call returns after queueing and hgrms_wait finishes it
+// (only for images the device reads directly: nothing is copied back on the
+// host).
 int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int max_k, int* k_out,
-               const Tuning& tu, bool write_back, float* ms, int forced_fused = 0) {
+               const Tuning& tu, bool write_back, float* ms, int forced_fused = 0, bool async_call = false) {
     const int T = tu.T;
     const hg::FusedEntry* fe = find_fused(beta, T);
     if (!fe) return HGRMS_EINVAL;
@@ -523,10 +540,38 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
     HG_TRY(h, cudaMemcpyAsync(h->host_ctrl, h->ctrl, sizeof(hg::Ctrl), cudaMemcpyDeviceToHost, s));
     if (per_image_k)
         HG_TRY(h, cudaMemcpyAsync(h->host_img_k, h->img_k, (size_t)n * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    hgrms_ctx::PendingCall pd;
+    pd.n = n;
+    pd.max_k = max_k;
+    pd.launches = launches;
+    pd.fused_launches = fused_launches;
+    pd.T = T;
+    pd.eval_max = tu.eval_max;
+    pd.TH = fe->TH;
+    pd.TW = fe->TW;
+    pd.tiles_total = tiles_total;
+    pd.per_image_k = per_image_k;
+    pd.write_back = write_back;
+    pd.timed = timed;
+    if (async_call) {
+        pd.active = true;
+        h->pending = pd;
+        return HGRMS_OK;
+    }
     HG_TRY(h, cudaStreamSynchronize(s));
+    return finish_hybrid(h, pd, im, k_out, ms);
+}
+
+// The host side of a hybrid call after its queued work finished: copy host
+// images back (synchronous calls only), read k, the launch times and the
+// statistics.  `im` may be null when every image was device-readable.
+int finish_hybrid(hgrms_ctx* h, const hgrms_ctx::PendingCall& pd, const BatchImg* im, int* k_out, float* ms) {
+    cudaStream_t s = h->stream;
+    const int n = pd.n, max_k = pd.max_k, launches = pd.launches, fused_launches = pd.fused_launches;
+    const bool per_image_k = pd.per_image_k, write_back = pd.write_back, timed = pd.timed;
     const hg::Ctrl c = *h->host_ctrl;
     bool host_out = false;
-    for (int i = 0; i < n && write_back && max_k > 0; ++i) {
+    for (int i = 0; im && i < n && write_back && max_k > 0; ++i) {
         if (im[i].dev) continue;
         const hg::ImgDesc& d = h->host_desc[i];
         HG_TRY(h, cudaMemcpy2DAsync(im[i].ptr, (size_t)d.cols,
@@ -558,11 +603,11 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
     }
     for (int i = 0; i < n; ++i) k_out[i] = per_image_k ? (int)h->host_img_k[i] : (int)c.k;
     h->stats.launches += launches;
-    h->stats.passes_per_launch = T;
-    h->stats.tile_eval_max = tu.eval_max;
-    h->stats.tile_rows = fe->TH;
-    h->stats.tile_cols = fe->TW;
-    h->stats.ctas_per_launch += tiles_total;
+    h->stats.passes_per_launch = pd.T;
+    h->stats.tile_eval_max = pd.eval_max;
+    h->stats.tile_rows = pd.TH;
+    h->stats.tile_cols = pd.TW;
+    h->stats.ctas_per_launch += pd.tiles_total;
     h->stats.passes_executed += (int)c.executed;
     h->stats.evals_fused += (long long)c.evals_fused;
     h->stats.evals_list += (long long)c.evals_list;
@@ -836,7 +881,7 @@ HG_EXPORT void hgrms_destroy(hgrms_t h) {
     if (!h) return;
     {
         DeviceGuard g(h->device);
-        if (h->stream) cudaStreamSynchronize(h->stream);
+        if (h->stream || h->pending.active) cudaStreamSynchronize(h->stream);
         for (int i = 0; i < 3; ++i)
             if (h->canvas[i]) cudaFree(h->canvas[i]);
         if (h->ctrl) cudaFree(h->ctrl);
@@ -863,6 +908,7 @@ HG_EXPORT void hgrms_destroy(hgrms_t h) {
 
 HG_EXPORT int hgrms_denoise(hgrms_t h, uint8_t* img, int rows, int cols, int alpha, int beta, int max_k) {
     if (!h || !img) return HGRMS_EINVAL;
+    if (h->pending.active) return HGRMS_EBUSY;
     int rc = check_args(rows, cols, alpha, beta, max_k);
     if (rc < 0) return rc;
     DeviceGuard g(h->device);
@@ -893,9 +939,52 @@ HG_EXPORT int hgrms_denoise(hgrms_t h, uint8_t* img, int rows, int cols, int alp
     return rc < 0 ? rc : k;
 }
 
+HG_EXPORT int hgrms_denoise_async(hgrms_t h, uint8_t* img, int rows, int cols, int alpha, int beta, int max_k) {
+    if (!h || !img) return HGRMS_EINVAL;
+    if (h->pending.active) return HGRMS_EBUSY;
+    int rc = check_args(rows, cols, alpha, beta, max_k);
+    if (rc < 0) return rc;
+    DeviceGuard g(h->device);
+    uint8_t* dp = nullptr;
+    if (pointer_kind(img, h->device, &dp) != 1) return HGRMS_EINVAL;  // must be device-readable
+    if (h->opt_kernel != kHybrid || h->opt_autotune || h->opt_predict_k) {
+        // Schedules that need the host between launches run now.
+        const int k = hgrms_denoise(h, img, rows, cols, alpha, beta, max_k);
+        if (k < 0) return k;
+        h->pending = hgrms_ctx::PendingCall{};
+        h->pending.active = true;
+        h->pending.done = true;
+        h->pending.result = k;
+        return HGRMS_OK;
+    }
+    h->stats = hgrms_stats_t{};
+    h->stats.k_pred = -1.0;
+    h->launch_ms.clear();
+    h->launch_kind.clear();
+    const BatchImg bi{dp, rows, cols, true};
+    int k = 0;
+    Tuning tu;
+    rc = choose_tuning(h, &bi, 1, alpha, beta, max_k, &k, &tu);
+    if (rc < 0) return rc;
+    return run_hybrid(h, &bi, 1, alpha, beta, max_k, &k, tu, true, nullptr, 0, true);
+}
+
+HG_EXPORT int hgrms_wait(hgrms_t h) {
+    if (!h || !h->pending.active) return HGRMS_EINVAL;
+    const hgrms_ctx::PendingCall pd = h->pending;
+    h->pending = hgrms_ctx::PendingCall{};
+    if (pd.done) return pd.result;
+    DeviceGuard g(h->device);
+    HG_TRY(h, cudaStreamSynchronize(h->stream));
+    int k = 0;
+    const int rc = finish_hybrid(h, pd, nullptr, &k, nullptr);
+    return rc < 0 ? rc : k;
+}
+
 HG_EXPORT int hgrms_denoise_batch(hgrms_t h, uint8_t* const* imgs, const int* rows, const int* cols, int n,
                                   int alpha, int beta, int max_k, int* k_out) {
     if (!h || n < 0 || (n > 0 && (!imgs || !rows || !cols || !k_out))) return HGRMS_EINVAL;
+    if (h->pending.active) return HGRMS_EBUSY;
     DeviceGuard g(h->device);
     std::vector<BatchImg> bi((size_t)n);
     for (int i = 0; i < n; ++i) {
@@ -1012,6 +1101,7 @@ HG_EXPORT const char* hgrms_strerror(int code) {
         case HGRMS_ENODEV: return "no CUDA device";
         case HGRMS_ETOOBIG: return "image too large for the fixed scratch of hgrms_denoise_noalloc";
         case HGRMS_EAGAIN: return "request not finished yet";
+        case HGRMS_EBUSY: return "an asynchronous call on this handle has not been waited for";
         default: return code >= 0 ? "success" : "unknown error";
     }
 }

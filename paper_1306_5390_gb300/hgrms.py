@@ -25,6 +25,7 @@ HGRMS_ETIMEOUT = -4
 HGRMS_ENODEV = -5
 HGRMS_ETOOBIG = -6
 HGRMS_EAGAIN = -7
+HGRMS_EBUSY = -8
 HGRMS_NOALLOC_SCRATCH_BYTES = 16 << 20
 
 HGRMS_OPT_KERNEL = 1
@@ -40,7 +41,7 @@ HGRMS_OPT_LIST_CTAS = 10
 
 # Every symbol the header declares (the CPU tests check the library exports them).
 EXPORTED = (
-    "hgrms_create", "hgrms_destroy", "hgrms_denoise", "hgrms_denoise_batch",
+    "hgrms_create", "hgrms_destroy", "hgrms_denoise", "hgrms_denoise_batch", "hgrms_denoise_async", "hgrms_wait",
     "hgrms_converged", "hgrms_strerror", "hgrms_last_cuda_error", "hgrms_set_option",
     "hgrms_stats", "hgrms_launch_times", "hgrms_default_passes", "hgrms_has_kernel",
     "hgrms_denoise_noalloc", "hgrms_server_create", "hgrms_server_submit", "hgrms_server_wait",
@@ -115,6 +116,10 @@ def load_library(path: str | None = None):
         lib.hgrms_destroy.restype = None
         lib.hgrms_denoise.argtypes = [vp, vp] + [ctypes.c_int] * 5
         lib.hgrms_denoise.restype = ctypes.c_int
+        lib.hgrms_denoise_async.argtypes = [vp, vp] + [ctypes.c_int] * 5
+        lib.hgrms_denoise_async.restype = ctypes.c_int
+        lib.hgrms_wait.argtypes = [vp]
+        lib.hgrms_wait.restype = ctypes.c_int
         lib.hgrms_denoise_batch.argtypes = [vp, ctypes.POINTER(vp), ip, ip] + [ctypes.c_int] * 4 + [ip]
         lib.hgrms_denoise_batch.restype = ctypes.c_int
         lib.hgrms_converged.argtypes = [vp]
@@ -178,6 +183,16 @@ def hgrms_destroy(h) -> None:
 def hgrms_denoise(h, img_ptr: int, rows: int, cols: int, alpha: int, beta: int, max_k: int) -> int:
     """Raw call: returns k or a negative code (not raised)."""
     return load_library().hgrms_denoise(h, img_ptr, rows, cols, alpha, beta, max_k)
+
+
+def hgrms_denoise_async(h, img_ptr: int, rows: int, cols: int, alpha: int, beta: int, max_k: int) -> int:
+    """Raw call: queues the call; returns 0 or a negative code (not raised)."""
+    return load_library().hgrms_denoise_async(h, img_ptr, rows, cols, alpha, beta, max_k)
+
+
+def hgrms_wait(h) -> int:
+    """Raw call: k of the queued call, or a negative code (not raised)."""
+    return load_library().hgrms_wait(h)
 
 
 def hgrms_denoise_batch(h, ptrs, rows, cols, alpha: int, beta: int, max_k: int, k_out) -> int:
@@ -298,6 +313,22 @@ class Denoiser:
         k = hgrms_denoise(self.h, ptr, rows, cols, alpha, beta, max_k)
         if k < 0:
             raise HgrmsError(k, "hgrms_denoise")
+        return k
+
+    def denoise_async(self, img, alpha: int, beta: int, max_k: int) -> None:
+        """Queue the in-place denoising of ``img`` (a CUDA tensor, or page-locked
+        host memory the device can read) on the handle's stream; ``wait()``
+        returns k."""
+        ptr, rows, cols = self._ptr_shape(img)
+        rc = hgrms_denoise_async(self.h, ptr, rows, cols, alpha, beta, max_k)
+        if rc < 0:
+            raise HgrmsError(rc, "hgrms_denoise_async")
+
+    def wait(self) -> int:
+        """Finish the call queued by ``denoise_async``; returns its k."""
+        k = hgrms_wait(self.h)
+        if k < 0:
+            raise HgrmsError(k, "hgrms_wait")
         return k
 
     def denoise_batch(self, imgs, alpha: int, beta: int, max_k: int):

@@ -47,7 +47,7 @@ def test_every_declared_symbol_is_exported(lib):
 def test_strerror(lib):
     from paper_1306_5390_gb300 import hgrms
     assert hgrms.strerror(0) == "success"
-    for code in (-1, -2, -3, -4, -5):
+    for code in (-1, -2, -3, -4, -5, -6, -7, -8):
         assert hgrms.strerror(code) not in ("success", "unknown error")
     assert hgrms.strerror(-99) == "unknown error"
 
@@ -65,6 +65,8 @@ def test_null_handle_errors_without_device_work(lib):
     lib.hgrms_destroy(None)  # accepted
     ks = [0]
     assert hgrms.hgrms_denoise_batch(None, [ctypes.addressof(buf)], [4], [4], 10, 1, 5, ks) == hgrms.HGRMS_EINVAL
+    assert lib.hgrms_denoise_async(None, ctypes.addressof(buf), 4, 4, 10, 1, 5) == hgrms.HGRMS_EINVAL
+    assert lib.hgrms_wait(None) == hgrms.HGRMS_EINVAL
 
 
 def test_kernel_table(lib):
