@@ -54,6 +54,8 @@ def parse_args(argv=None):
     p.add_argument("--max-k", type=int, default=32,
                    help="cap on changing passes (5 = the paper's fixed iteration factor)")
     p.add_argument("--passes", type=int, default=0, help="fused passes per launch (0 = built-in)")
+    p.add_argument("--graph", type=int, default=0, choices=(0, 1),
+                   help="1 = replay each call's recorded CUDA graph (HGRMS_OPT_GRAPH)")
     p.add_argument("--kernel", type=int, default=0,
                    help="0 fused tile launch + list passes (default), 1 unfused, 2 fused tile launches only")
     p.add_argument("--size", type=int, default=8192, help="side of the square image (8192 workload)")
@@ -190,6 +192,8 @@ def run_ours(args, rank, world, local):
     # with hgrms_denoise_async and then waits for each, so consecutive calls
     # run back to back on the device (no host round trip between them).
     ds = [hgrms.Denoiser(local, kernel=args.kernel, passes=args.passes, timing=True) for _ in betas]
+    for dd in ds:
+        dd.set_option(hgrms.HGRMS_OPT_GRAPH, args.graph)
     d = ds[0]
 
     def step(per_beta, ks):
@@ -338,6 +342,7 @@ def run_ours(args, rank, world, local):
         "data": "synthetic (seeded Gaussian-bump + gradient content, salt-and-pepper noise)",
         "config": {"workload": w["name"], "parallelism": f"replicas{world}" if world > 1 else "single",
                    "l2": f"{L2_FLUSH_BYTES >> 20} MiB buffer written before every timed step",
+                   "graph_replay": bool(args.graph),
                    "schedule": {0: "fused tile launch + list passes", 1: "unfused", 2: "fused tile launches"}[
                        args.kernel], "rows": rows, "cols": cols},
         "roofline": roofline,

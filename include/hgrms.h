@@ -295,6 +295,13 @@ int hgrms_predictor_grad(hgrms_t h, const float* weights, const float* x0, const
                                   ceil(k_hat / T) fused launches unconditionally (each stops once a pass
                                   changes nothing) before the list passes; the results and k do not
                                   depend on the estimate */
+#define HGRMS_OPT_GRAPH    11 /* 1 = the default schedule records the device work of a call on images
+                                   the device reads directly into a CUDA graph and replays it for later
+                                   calls with identical arguments (same pointers, sizes, parameters and
+                                   options): one graph launch instead of the call's separate launches,
+                                   copies and clears; up to 8 graphs per handle, the oldest dropped
+                                   first.  Results are identical either way; a call the graph cannot
+                                   record runs as usual. */
 #define HGRMS_OPT_LIST_CTAS 10 /* CTAs of the list-pass launch (0 = built-in: one per SM below
                                    16 M pixels, else as many as can be co-resident, 2 per SM) */
 #define HGRMS_OPT_TILE_EVAL_MAX 7 /* fused kernel: a pass runs as an in-tile list pass while the previous
@@ -332,6 +339,8 @@ typedef struct hgrms_stats {
                                choice was already known) */
     double k_pred;          /* HGRMS_OPT_PREDICT_K: the largest predicted k of the call's
                                images, else -1 */
+    int    graph;           /* HGRMS_OPT_GRAPH: 1 = the call replayed a recorded graph, 2 = it
+                               recorded one (and ran it), 0 = no graph */
 } hgrms_stats_t;
 
 int hgrms_stats(hgrms_t h, hgrms_stats_t* out);

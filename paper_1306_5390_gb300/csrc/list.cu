@@ -546,10 +546,19 @@ cudaError_t launch_loop_b(const PassArgs& a, int sms, cudaStream_t s) {
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     unsigned grid = (unsigned)(sms * (per_sm < 2 ? per_sm : 2));
     if (a.list_ctas > 0 && (unsigned)a.list_ctas < grid) grid = (unsigned)a.list_ctas;
-    PassArgs arg = a;
-    void* params[] = {&arg};
-    return cudaLaunchCooperativeKernel((const void*)list_loop_kernel<B, kBatch>, dim3(grid), dim3(kListThreads),
-                                       params, 0, s);
+    // A cooperative launch (all CTAs co-resident), in the form that stream
+    // capture into a CUDA graph accepts.
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kListThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, list_loop_kernel<B, kBatch>, a);
 }
 
 template <int B>

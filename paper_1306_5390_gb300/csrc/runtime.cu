@@ -93,6 +93,13 @@ struct hgrms_ctx {
     hg::ImgDesc* pred_desc = nullptr;
     int pred_desc_cap = 0;
     int opt_predict_k = 0;
+    // HGRMS_OPT_GRAPH: captured CUDA graphs of whole hybrid calls, by the
+    // bytes of everything the call's device work depends on (oldest first),
+    // and the stream they are captured on (the legacy default stream cannot
+    // be captured).
+    int opt_graph = 0;
+    std::vector<std::pair<std::vector<uint8_t>, cudaGraphExec_t>> graphs;
+    cudaStream_t cap_stream = nullptr;
     // The call that hgrms_denoise_async queued and hgrms_wait has not yet
     // finished (see PendingCall).
     struct PendingCall {
@@ -138,6 +145,7 @@ namespace {
 // for wider windows, whose fused passes cost more than list passes even on
 // dense change sets.  With HGRMS_OPT_RELAUNCH_PPM set, up to 8 for any beta.
 constexpr int kDefaultRelaunches = 3;
+constexpr size_t kMaxGraphs = 8;  // captured graphs kept per handle (HGRMS_OPT_GRAPH)
 constexpr int kMaxRelaunches = 8;
 long long default_relaunch_ppm(int beta) {
     return beta == 1 ? 25000 : 1000000;
@@ -444,21 +452,6 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
         h->table_cache.assign(h->host_desc, h->host_desc + n);
         h->table_tiles = (int)tiles_total;
     }
-    if (ms) HG_TRY(h, cudaEventRecord(h->tune_ev[0], s));
-    // Images in: the first fused launch reads the images the device can read
-    // (device memory, mapped page-locked host memory) directly; other host
-    // images are copied into canvas 0, which it reads for them.
-    for (int i = 0; i < n; ++i) {
-        if (im[i].dev) continue;
-        const hg::ImgDesc& d = h->host_desc[i];
-        HG_TRY(h, cudaMemcpy2DAsync(h->canvas[0] + d.off + (long long)hg::kPadY * d.pitch + hg::kPadX, (size_t)d.pitch,
-                                    im[i].ptr, (size_t)d.cols, (size_t)d.cols, (size_t)d.rows,
-                                    cudaMemcpyHostToDevice, s));
-    }
-    HG_TRY(h, hg::launch_ctrl_init(h->ctrl, (unsigned)max_k, s));
-    HG_TRY(h, cudaMemsetAsync(h->bitmaps, 0, 4 * (size_t)bm_total * sizeof(uint32_t), s));
-    HG_TRY(h, cudaMemsetAsync(h->bar, 0, sizeof(hg::GridBar), s));
-    if (per_image_k) HG_TRY(h, cudaMemsetAsync(h->img_k, 0, (size_t)n * sizeof(unsigned), s));
     hg::PassArgs a;
     memset(&a, 0, sizeof(a));
     for (int i = 0; i < 3; ++i) a.canvas[i] = h->canvas[i];
@@ -513,33 +506,104 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
         rc = ensure_events(h, 2 * (size_t)launches);
         if (rc < 0) return rc;
     }
-    for (int i = 0; i < launches; ++i) {
-        if (timed) HG_TRY(h, cudaEventRecord(h->events[2 * i], s));
-        if (i < fused_launches) {
-            HG_TRY(h, fe->launch(a, (int)tiles_total, s));
-        } else if (h->coop_stream) {
-            HG_TRY(h, cudaEventRecord(h->coop_ev[0], s));
-            HG_TRY(h, cudaStreamWaitEvent(h->coop_stream, h->coop_ev[0], 0));
-            HG_TRY(h, hg::launch_list(beta, a, h->sms, h->coop_stream));
-            HG_TRY(h, cudaEventRecord(h->coop_ev[1], h->coop_stream));
-            HG_TRY(h, cudaStreamWaitEvent(s, h->coop_ev[1], 0));
-        } else {
-            HG_TRY(h, hg::launch_list(beta, a, h->sms, s));
+    // The call's device work, on stream `st` (the handle's stream, or the
+    // capture stream while a graph is recorded).
+    auto enqueue = [&](cudaStream_t st, bool capturing) -> int {
+        cudaStream_t s = st;
+        // Timing events inside a recorded graph must be record nodes (an
+        // ordinary record during capture only orders the capture).
+        auto record = [&](cudaEvent_t e) {
+            return capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+        };
+        // Images in: the first fused launch reads the images the device can read
+        // (device memory, mapped page-locked host memory) directly; other host
+        // images are copied into canvas 0, which it reads for them.
+        for (int i = 0; i < n; ++i) {
+            if (im[i].dev) continue;
+            const hg::ImgDesc& d = h->host_desc[i];
+            HG_TRY(h, cudaMemcpy2DAsync(h->canvas[0] + d.off + (long long)hg::kPadY * d.pitch + hg::kPadX, (size_t)d.pitch,
+                                        im[i].ptr, (size_t)d.cols, (size_t)d.cols, (size_t)d.rows,
+                                        cudaMemcpyHostToDevice, s));
         }
-        if (timed) HG_TRY(h, cudaEventRecord(h->events[2 * i + 1], s));
-    }
-    if (!write_back || max_k == 0) {
-        // a trial, or no pass ran (the images are unchanged): no copy-out
-    } else if (n == 1 && im[0].dev) {
-        HG_TRY(h, hg::launch_copy_out(h->ctrl, h->canvas, h->host_desc[0].pitch, im[0].ptr, im[0].rows, im[0].cols,
-                                      h->sms, s));
+        HG_TRY(h, hg::launch_ctrl_init(h->ctrl, (unsigned)max_k, s));
+        HG_TRY(h, cudaMemsetAsync(h->bitmaps, 0, 4 * (size_t)bm_total * sizeof(uint32_t), s));
+        HG_TRY(h, cudaMemsetAsync(h->bar, 0, sizeof(hg::GridBar), s));
+        if (per_image_k) HG_TRY(h, cudaMemsetAsync(h->img_k, 0, (size_t)n * sizeof(unsigned), s));
+        for (int i = 0; i < launches; ++i) {
+            if (timed) HG_TRY(h, record(h->events[2 * i]));
+            if (i < fused_launches) {
+                HG_TRY(h, fe->launch(a, (int)tiles_total, s));
+            } else if (h->coop_stream) {
+                HG_TRY(h, cudaEventRecord(h->coop_ev[0], s));
+                HG_TRY(h, cudaStreamWaitEvent(h->coop_stream, h->coop_ev[0], 0));
+                HG_TRY(h, hg::launch_list(beta, a, h->sms, h->coop_stream));
+                HG_TRY(h, cudaEventRecord(h->coop_ev[1], h->coop_stream));
+                HG_TRY(h, cudaStreamWaitEvent(s, h->coop_ev[1], 0));
+            } else {
+                HG_TRY(h, hg::launch_list(beta, a, h->sms, s));
+            }
+            if (timed) HG_TRY(h, record(h->events[2 * i + 1]));
+        }
+        if (!write_back || max_k == 0) {
+            // a trial, or no pass ran (the images are unchanged): no copy-out
+        } else if (n == 1 && im[0].dev) {
+            HG_TRY(h, hg::launch_copy_out(h->ctrl, h->canvas, h->host_desc[0].pitch, im[0].ptr, im[0].rows, im[0].cols,
+                                          h->sms, s));
+        } else {
+            HG_TRY(h, hg::launch_copy_out_batch(h->ctrl, h->canvas, h->d_desc, n, max_words, h->sms, s));
+        }
+        HG_TRY(h, cudaMemcpyAsync(h->host_ctrl, h->ctrl, sizeof(hg::Ctrl), cudaMemcpyDeviceToHost, s));
+        if (per_image_k)
+            HG_TRY(h, cudaMemcpyAsync(h->host_img_k, h->img_k, (size_t)n * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+        return HGRMS_OK;
+    };
+    if (ms) HG_TRY(h, cudaEventRecord(h->tune_ev[0], s));
+    bool all_dev = true;
+    for (int i = 0; i < n; ++i) all_dev = all_dev && im[i].dev;
+    if (h->opt_graph && !ms && !h->coop_stream && all_dev) {
+        // Replay the graph of an identical earlier call, or record one.
+        std::vector<uint8_t> key(sizeof(a) + 16 * sizeof(long long));
+        memcpy(key.data(), &a, sizeof(a));
+        const long long extra[16] = {beta, T, fused_launches, list_loop, launches, write_back, max_k, n,
+                                     (long long)(uintptr_t)im[0].ptr, im[0].rows, im[0].cols, max_words,
+                                     timed, bm_total, (long long)(uintptr_t)h->host_ctrl,
+                                     (long long)(uintptr_t)h->host_img_k};
+        memcpy(key.data() + sizeof(a), extra, sizeof(extra));
+        cudaGraphExec_t ex = nullptr;
+        for (auto& g : h->graphs)
+            if (g.first == key) ex = g.second;
+        if (ex) {
+            h->stats.graph = 1;
+        } else {
+            if (!h->cap_stream) HG_TRY(h, cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
+            HG_TRY(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeRelaxed));
+            const int erc = enqueue(h->cap_stream, true);
+            cudaGraph_t g = nullptr;
+            const cudaError_t ee = cudaStreamEndCapture(h->cap_stream, &g);
+            if (erc == HGRMS_OK && ee == cudaSuccess && g && cudaGraphInstantiate(&ex, g, 0) == cudaSuccess) {
+                if (h->graphs.size() >= kMaxGraphs) {
+                    cudaGraphExecDestroy(h->graphs.front().second);
+                    h->graphs.erase(h->graphs.begin());
+                }
+                h->graphs.emplace_back(std::move(key), ex);
+                h->stats.graph = 2;
+            } else {
+                ex = nullptr;
+                (void)cudaGetLastError();  // a failed capture falls back to plain launches
+            }
+            if (g) cudaGraphDestroy(g);
+        }
+        if (ex) {
+            HG_TRY(h, cudaGraphLaunch(ex, s));
+        } else {
+            rc = enqueue(s, false);
+            if (rc < 0) return rc;
+        }
     } else {
-        HG_TRY(h, hg::launch_copy_out_batch(h->ctrl, h->canvas, h->d_desc, n, max_words, h->sms, s));
+        rc = enqueue(s, false);
+        if (rc < 0) return rc;
     }
     if (ms) HG_TRY(h, cudaEventRecord(h->tune_ev[1], s));
-    HG_TRY(h, cudaMemcpyAsync(h->host_ctrl, h->ctrl, sizeof(hg::Ctrl), cudaMemcpyDeviceToHost, s));
-    if (per_image_k)
-        HG_TRY(h, cudaMemcpyAsync(h->host_img_k, h->img_k, (size_t)n * sizeof(unsigned), cudaMemcpyDeviceToHost, s));
     hgrms_ctx::PendingCall pd;
     pd.n = n;
     pd.max_k = max_k;
@@ -900,6 +964,8 @@ HG_EXPORT void hgrms_destroy(hgrms_t h) {
             if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : h->coop_ev)
             if (e) cudaEventDestroy(e);
+        for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
+        if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
         for (hg::Predictor* p : h->pred) hg::predictor_free(p);
         if (h->pred_desc) cudaFree(h->pred_desc);
     }
@@ -1141,6 +1207,10 @@ HG_EXPORT int hgrms_set_option(hgrms_t h, int option, int value) {
         case HGRMS_OPT_PREDICT_K:
             if (value != 0 && value != 1) return HGRMS_EINVAL;
             h->opt_predict_k = value;
+            return HGRMS_OK;
+        case HGRMS_OPT_GRAPH:
+            if (value != 0 && value != 1) return HGRMS_EINVAL;
+            h->opt_graph = value;
             return HGRMS_OK;
         case HGRMS_OPT_LIST_CTAS:
             if (value < 0) return HGRMS_EINVAL;

@@ -38,6 +38,7 @@ HGRMS_OPT_TILE_EVAL_MAX = 7
 HGRMS_OPT_AUTOTUNE = 8
 HGRMS_OPT_PREDICT_K = 9
 HGRMS_OPT_LIST_CTAS = 10
+HGRMS_OPT_GRAPH = 11
 
 # Every symbol the header declares (the CPU tests check the library exports them).
 EXPORTED = (
@@ -80,6 +81,7 @@ class hgrms_stats_t(ctypes.Structure):
         ("autotuned", ctypes.c_int),
         ("tune_ms", ctypes.c_double),
         ("k_pred", ctypes.c_double),
+        ("graph", ctypes.c_int),
     ]
 
     def as_dict(self):
