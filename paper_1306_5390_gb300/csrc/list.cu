@@ -233,6 +233,15 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
             ctrl->list_n[(t + base + 2) & 3] = 0u;
         }
         const unsigned n = n_cur, nclr = n_last;
+        // The first list entry this thread reads (beta 1: pair warp_base +
+        // lane; wider windows: task tid * gridDim.x + blockIdx.x), loaded
+        // before the bitmap clearing below so that the two loads overlap.
+        uint32_t pk_first = 0u;
+        if (n <= a.list_cap) {
+            const long long i0 = B == 1 ? warp_base + lane : (long long)tid * gridDim.x + blockIdx.x;
+            const long long per = B == 1 ? P : W;
+            if (i0 < (long long)n * per) pk_first = __ldcg(prev + (unsigned)(i0 / per));
+        }
         // Clear bitmap sc (written by pass t - 2, read by pass t - 1) for pass
         // t + 2: walk its list, or clear it all if the list overflowed.
         {
@@ -257,7 +266,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
             const long long total = (long long)n * P;
             // The list entry of the next iteration is loaded one iteration early.
             long long i = warp_base + lane;
-            uint32_t pk = i < total ? __ldcg(prev + (unsigned)(i / P)) : 0u;
+            uint32_t pk = pk_first;
             for (long long base = warp_base; base < total; base += gthreads, i += gthreads) {
                 const long long inext = i + gthreads;
                 const uint32_t pk_next = inext < total ? __ldcg(prev + (unsigned)(inext / P)) : 0u;
@@ -338,7 +347,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
             // tasks than threads.
             const long long ntask = (long long)n * W;
             long long i = (long long)tid * gridDim.x + blockIdx.x;
-            uint32_t pk = i < ntask ? __ldcg(prev + (unsigned)(i / W)) : 0u;  // loaded one chunk early
+            uint32_t pk = pk_first;  // later chunks' entries are loaded one chunk early
             for (long long c0 = 0; c0 + blockIdx.x < ntask; c0 += gthreads, i += gthreads) {
                 const long long inext = i + gthreads;
                 const uint32_t pk_next = inext < ntask ? __ldcg(prev + (unsigned)(inext / W)) : 0u;
