@@ -154,6 +154,20 @@ struct PassArgs {
     int list_ctas;            // list-pass loop CTAs (0 = as many as can be co-resident)
 };
 
+// floor(sqrt(floor(sum / flag))) exactly (the root mean square of Algorithm
+// 2 in integers), for 0 <= sum <= flag * 255^2 and 1 <= flag <= 225, as every
+// kernel computes it.  sum < 2^24 and flag are exact in float; a non-integer
+// quotient is at least 1/flag below the next integer, far above the rounding
+// of the correctly rounded division at these magnitudes, so the floor of the
+// float quotient is floor(sum / flag); the square root is correctly rounded,
+// so its floor is the integer square root (the quotient is at most 255^2).
+// `sum` is passed as the float that holds it exactly.  Checked for every flag
+// and quotient through hgrms_rms.
+__device__ __forceinline__ int rms_floor(float sum, int flag) {
+    const float q = floorf(__fdiv_rn(sum, (float)flag));
+    return (int)floorf(__fsqrt_rn(q));
+}
+
 // Passes the launch must run: 0 when the call has finished.
 __device__ __forceinline__ int launch_passes(const Ctrl* c, int T) {
     unsigned k = __ldcg(&c->k);

@@ -246,10 +246,8 @@ __device__ __forceinline__ uint32_t candidate_mask(const uint32_t na, const uint
 
 // Exact Algorithm 2 for one interior pixel at tile position (y, x): returns
 // the replacement value, or -1 when the pixel is not replaced.  Values are
-// integers below 2^24, so float arithmetic is exact; floor(sum / flag) is
-// exact because a non-integer quotient is at least 1/flag from the next
-// integer, far above float rounding at these magnitudes, and the square
-// root is correctly rounded (floor of it is exact for arguments <= 65025).
+// integers below 2^24, so the float sums are exact; rms_floor turns them
+// into the integer root mean square.
 template <int B, int SW>
 __device__ __forceinline__ int exact_replacement(const __half* __restrict__ in, int y, int x, int alpha) {
     const float ip = __half2float(in[y * SW + x]);
@@ -267,10 +265,7 @@ __device__ __forceinline__ int exact_replacement(const __half* __restrict__ in, 
             flag += open ? 1 : 0;
         }
     constexpr int kPixCount = (2 * B + 1) * (2 * B + 1);
-    if (flag > kPixCount - 3) {
-        const float q = floorf(__fdiv_rn(sum, (float)flag));
-        return (int)floorf(__fsqrt_rn(q));
-    }
+    if (flag > kPixCount - 3) return rms_floor(sum, flag);
     return -1;
 }
 

@@ -32,6 +32,8 @@ cudaError_t launch_list(int beta, const PassArgs& a, int sms, cudaStream_t s);
 cudaError_t launch_copy_out_batch(const Ctrl* c, uint8_t* const arena[3], const ImgDesc* imgs, int nimg,
                                   long long max_words, int sms, cudaStream_t s);
 cudaError_t launch_tile_map(const ImgDesc* imgs, int nimg, int total_tiles, int* tile_img, cudaStream_t s);
+// out[i] = rms_floor(sum[i], flag[i]) (the kernels' integer root mean square).
+cudaError_t launch_rms(const int* sum, const int* flag, int* out, int n, cudaStream_t s);
 
 }  // namespace hg
 

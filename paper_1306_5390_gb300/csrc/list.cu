@@ -45,11 +45,7 @@ __device__ __forceinline__ uint32_t row_bits(const uint32_t* __restrict__ row, i
 
 // Algorithm 2 for an interior pixel (card <= 2 is implied by flag >
 // pix_count - 3 for alpha >= 1, and card is 0 for alpha = 0).  `p` points at
-// the pixel in a row-major byte array with row stride `stride`.  sum < 2^24
-// and flag <= 225, so the float quotient is exact to well under the gap to
-// the next integer and its floor is floor(sum / flag); the square root is
-// correctly rounded, so its floor is the integer square root (sum / flag is
-// at most 255^2).
+// the pixel in a row-major byte array with row stride `stride`.
 template <int B>
 __device__ __forceinline__ int eval_pixel(const uint8_t* p, long long stride, int alpha) {
     const int ip = p[0];
@@ -64,10 +60,7 @@ __device__ __forceinline__ int eval_pixel(const uint8_t* p, long long stride, in
             flag += open ? 1 : 0;
         }
     constexpr int kPixCount = (2 * B + 1) * (2 * B + 1);
-    if (flag > kPixCount - 3) {
-        const float q = floorf(__fdiv_rn((float)sum, (float)flag));
-        return (int)floorf(__fsqrt_rn(q));
-    }
+    if (flag > kPixCount - 3) return rms_floor((float)sum, flag);
     return ip;
 }
 
@@ -321,8 +314,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
                                 }
                             int nv = ip;
                             if (flag > P - 3) {
-                                const float qf = floorf(__fdiv_rn((float)sum, (float)flag));
-                                nv = (int)floorf(__fsqrt_rn(qf));
+                                nv = rms_floor((float)sum, flag);
                             }
                             out_arena[d.off + (long long)kPadY * d.pitch + kPadX + off] = (uint8_t)nv;
                             if (nv != ip) {
@@ -442,8 +434,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
                             }
                         int nv = ip;
                         if (flag > P - 3) {
-                            const float qf = floorf(__fdiv_rn((float)sum, (float)flag));
-                            nv = (int)floorf(__fsqrt_rn(qf));
+                            nv = rms_floor((float)sum, flag);
                         }
                         out_arena[d.off + (long long)kPadY * d.pitch + kPadX + off] = (uint8_t)nv;
                         if (nv != ip) {

@@ -245,6 +245,18 @@ cudaError_t launch_copy_out_batch(const Ctrl* c, uint8_t* const arena[3], const 
     return cudaGetLastError();
 }
 
+__global__ void rms_kernel(const int* __restrict__ sum, const int* __restrict__ flag, int* __restrict__ out, int n) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
+        out[i] = rms_floor((float)sum[i], flag[i]);
+}
+
+cudaError_t launch_rms(const int* sum, const int* flag, int* out, int n, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int blocks = (n + 255) / 256 < 4096 ? (n + 255) / 256 : 4096;
+    rms_kernel<<<blocks, 256, 0, s>>>(sum, flag, out, n);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_tile_map(const ImgDesc* imgs, int nimg, int total_tiles, int* tile_img, cudaStream_t s) {
     if (nimg <= 0) return cudaSuccess;
     tile_map_kernel<<<(unsigned)nimg, 256, 0, s>>>(imgs, nimg, total_tiles, tile_img);

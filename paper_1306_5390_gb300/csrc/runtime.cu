@@ -1244,6 +1244,14 @@ HG_EXPORT int hgrms_launch_times(hgrms_t h, float* ms, int* kind, int n) {
     return m;
 }
 
+HG_EXPORT int hgrms_rms(const int* sum, const int* flag, int* out, int n, void* cuda_stream) {
+    if (n < 0 || (n > 0 && (!sum || !flag || !out))) return HGRMS_EINVAL;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    cudaError_t e = hg::launch_rms(sum, flag, out, n, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    return e == cudaSuccess ? HGRMS_OK : HGRMS_ECUDA;
+}
+
 HG_EXPORT int hgrms_default_passes(int beta) {
     if (beta < 1 || beta > hg::kMaxBeta) return HGRMS_EINVAL;
     return default_passes(beta);

@@ -47,7 +47,7 @@ EXPORTED = (
     "hgrms_stats", "hgrms_launch_times", "hgrms_default_passes", "hgrms_has_kernel",
     "hgrms_denoise_noalloc", "hgrms_server_create", "hgrms_server_submit", "hgrms_server_wait",
     "hgrms_server_stats", "hgrms_server_destroy", "hgrms_predictor_load", "hgrms_predict_k",
-    "hgrms_predictor_train", "hgrms_predictor_grad",
+    "hgrms_predictor_train", "hgrms_predictor_grad", "hgrms_rms",
 )
 
 PREDICTOR_WEIGHTS = 9 * 16 + 3 * 9 * 16 * 16 + 4 * 16 + 33  # floats per network
@@ -138,6 +138,8 @@ def load_library(path: str | None = None):
         lib.hgrms_launch_times.restype = ctypes.c_int
         lib.hgrms_denoise_noalloc.argtypes = [vp] + [ctypes.c_int] * 5 + [vp]
         lib.hgrms_denoise_noalloc.restype = ctypes.c_int
+        lib.hgrms_rms.argtypes = [vp, vp, vp, ctypes.c_int, vp]
+        lib.hgrms_rms.restype = ctypes.c_int
         lib.hgrms_default_passes.argtypes = [ctypes.c_int]
         lib.hgrms_default_passes.restype = ctypes.c_int
         lib.hgrms_has_kernel.argtypes = [ctypes.c_int, ctypes.c_int]

@@ -286,3 +286,26 @@ def test_8192_full_size_sampled(oracle_mod, den, torch_cuda, beta):
         # A converged result is a fixed point: one more pass changes nothing.
         t2 = torch.from_numpy(out).cuda()
         assert den.denoise(t2, w["alpha"], beta, 1) == 0
+
+
+def test_rms_arithmetic_exhaustive(torch_cuda):
+    """The kernels' integer root mean square, floor(sqrt(floor(sum / flag))),
+    against exact integer math for every flag 1..225 and every quotient
+    0..255^2, at both ends of the quotient's range of sums (q * flag and
+    q * flag + flag - 1), through the C ABI."""
+    import math
+    from paper_1306_5390_gb300 import hgrms
+    torch = torch_cuda
+    lib = hgrms.load_library()
+    isq = np.array([math.isqrt(q) for q in range(255 * 255 + 1)], dtype=np.int32)
+    q = torch.arange(0, 255 * 255 + 1, dtype=torch.int32, device="cuda")
+    for flag in range(1, 226):
+        for r in (0, flag - 1):
+            s = q * flag + r
+            keep = s <= flag * 255 * 255
+            s = s[keep].contiguous()
+            f = torch.full_like(s, flag)
+            out = torch.empty_like(s)
+            assert lib.hgrms_rms(s.data_ptr(), f.data_ptr(), out.data_ptr(), s.numel(), None) == 0
+            expect = isq[(s.cpu().numpy() // flag)]
+            assert np.array_equal(out.cpu().numpy(), expect), (flag, r)
