@@ -292,8 +292,9 @@ int hgrms_predictor_grad(hgrms_t h, const float* weights, const float* x0, const
 #define HGRMS_OPT_RELAUNCH_PPM 6 /* default schedule: after a fused launch, another fused launch runs
                                     (instead of list passes) while a list pass would evaluate more than
                                     this many pixels per million pixels of the call, up to 8 times
-                                    (0 = built-in: 25000 for beta 1, up to 3 times, never for
-                                    beta >= 2; 1000000 or more = never) */
+                                    (0 = built-in: 25000 for beta 1, up to 3 times, for calls of
+                                    at least 4 Mi pixels; never for beta >= 2 or smaller calls;
+                                    1000000 or more = never) */
 #define HGRMS_OPT_AUTOTUNE 8 /* 1 = choose the fused passes per launch and the in-tile switch point
                                  by timing: the first call of each (beta, single image or batch,
                                  size class = bit length of the pixel count) runs every compiled

@@ -145,6 +145,7 @@ namespace {
 // for wider windows, whose fused passes cost more than list passes even on
 // dense change sets.  With HGRMS_OPT_RELAUNCH_PPM set, up to 8 for any beta.
 constexpr int kDefaultRelaunches = 3;
+constexpr long long kRelaunchMinPixels = 4ll << 20;
 constexpr size_t kMaxGraphs = 8;  // captured graphs kept per handle (HGRMS_OPT_GRAPH)
 constexpr int kMaxRelaunches = 8;
 long long default_relaunch_ppm(int beta) {
@@ -488,7 +489,12 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
     const bool user_ppm = h->opt_relaunch_ppm > 0;
     const long long ppm = user_ppm ? h->opt_relaunch_ppm : default_relaunch_ppm(beta);
     a.relaunch_evals = ppm >= 1000000 ? (1ll << 62) : px_total / 1000000 * ppm + px_total % 1000000 * ppm / 1000000;
-    int relaunches = ppm >= 1000000 ? 0 : (user_ppm ? kMaxRelaunches : kDefaultRelaunches);
+    // Built-in: relaunch slots only for calls of at least kRelaunchMinPixels
+    // (below that the list passes are cheap, and each slot a launch that
+    // usually finds nothing to do: ~5 us of a ~100 us call on 256 x 256).
+    int relaunches = ppm >= 1000000 ? 0
+                                    : (user_ppm ? kMaxRelaunches
+                                                : (px_total >= kRelaunchMinPixels ? kDefaultRelaunches : 0));
     if (forced_fused > 0) {
         // A predicted k: that many passes run as fused launches (each still
         // stops once a pass changed nothing), the list passes do the rest.
