@@ -330,6 +330,11 @@ def run_ours(args, rank, world, local):
     if roofline["traffic"]:
         # DRAM bytes the kernel moves (ncu) over its measured launch time.
         roofline["hbm_achieved_frac"] = round(roofline["traffic"] / launch_s / 1e9 / peaks.get("hbm_gbs", 6800.0), 4)
+    # Share of issue slots the kernel used (ncu smsp__issue_active of the same
+    # summary): the comparisons it does per issued instruction, not idle
+    # hardware, are what the ALU fraction above reflects.
+    roofline["issue_active_frac"] = profile_metric(dom_name, dom_b, dom_T, rows, cols,
+                                                   "smsp__issue_active.avg.pct_of_peak_sustained_active", 0.01)
     pix_iters_per_step = units / max(1, args.steps) / world
     step_s = total_ms * 1e-3 / args.steps
     hbm_eff = 2.0 * pix_iters_per_step / step_s / 1e9
@@ -625,6 +630,29 @@ def traffic_from_profiles(name, beta, T, rows, cols):
     if sha != kernel_source_hash():
         return None
     return value
+
+
+def profile_metric(name, beta, T, rows, cols, metric, scale=1.0):
+    """A metric of the dominant kernel's --set full section in its committed
+    ncu summary (times `scale`), or None when absent or stale."""
+    tag = f"{name}_b{beta}" + (f"_t{T}" if name == "fused_kernel" else "")
+    path = os.path.join(ROOT, "profiles", f"{tag}_{rows}x{cols}.txt")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    sha = None
+    for ln in text.splitlines():
+        if "source_sha256:" in ln:
+            sha = ln.split("source_sha256:", 1)[1].split()[0]
+    if sha != kernel_source_hash() or "# --set full capture of the same launch (first step):" not in text:
+        return None  # no capture of the current sources
+    for ln in text.splitlines():
+        if ln.startswith(metric + ":"):
+            try:
+                return round(float(ln.split(":", 1)[1].split()[0]) * scale, 4)
+            except ValueError:
+                return None
+    return None
 
 
 def oracle_sample(w, band_rows, first_row=0):
