@@ -1,0 +1,57 @@
+"""CPU checks of the integer identities the fused kernel's packed count
+relies on (the kernel itself is checked bit-exactly against the oracle by the
+GPU parity tests).
+
+The dense passes sum the 0/1 results of the fp16 closed-neighbour test as
+32-bit integers: each result is the fp16 bit pattern 0x0000 or 0x3C00 in the
+low (pixel 2j) or high (pixel 2j + 1) half of a word.  After K_lo and K_hi
+closed neighbours the word, times 47 modulo 2^32, must have byte 1 equal to
+4 K_lo and byte 3 equal to 4 K_hi + (0..2), so that "at most one closed
+neighbour" is "byte & 0xF8 == 0"; and the SWAR test that marks the bytes
+with bit 7 must agree.  Both are checked for every K_lo, K_hi <= 48 (beta
+<= 3 has at most 48 neighbours)."""
+import itertools
+
+
+def packed_count(k_lo, k_hi):
+    return (k_lo * 0x3C00 + k_hi * 0x3C00 * 65536) % 2**32
+
+
+def test_decode_bytes_exhaustive():
+    for k_lo, k_hi in itertools.product(range(49), repeat=2):
+        z = packed_count(k_lo, k_hi) * 47 % 2**32
+        b1, b3 = (z >> 8) & 0xFF, (z >> 24) & 0xFF
+        assert b1 == 4 * k_lo, (k_lo, k_hi)
+        assert 4 * k_hi <= b3 <= 4 * k_hi + 2, (k_lo, k_hi)
+        assert ((b1 & 0xF8) == 0) == (k_lo <= 1)
+        assert ((b3 & 0xF8) == 0) == (k_hi <= 1)
+
+
+def test_swar_byte_test_exhaustive():
+    """((q & 0x78787878) + 0x7F7F7F7F | q) & 0x80808080 sets bit 7 of exactly
+    the bytes of q with (byte & 0xF8) != 0, for every byte value."""
+    for v in range(256):
+        for pos in range(4):
+            q = v << (8 * pos)
+            nz = (((q & 0x78787878) + 0x7F7F7F7F) | q) & 0x80808080
+            expect = (0x80 << (8 * pos)) if (v & 0xF8) else 0
+            assert nz == expect, (v, pos)
+    # four bytes at once (every combination of the four states that matter)
+    for bytes_ in itertools.product((0, 5, 7, 8, 0x80, 0xFF), repeat=4):
+        q = sum(b << (8 * i) for i, b in enumerate(bytes_))
+        nz = (((q & 0x78787878) + 0x7F7F7F7F) | q) & 0x80808080
+        assert nz == sum((0x80 << (8 * i)) for i, b in enumerate(bytes_) if b & 0xF8)
+
+
+def test_gather_of_bytes_1_and_3():
+    """The byte permute 0x7531 of (a, b) gathers bytes 1 and 3 of a, then of
+    b: pixels 0-3 of the 8-pixel segment from the words of pairs 0 and 1."""
+    def prmt(a, b, sel):
+        src = a | (b << 32)
+        out = 0
+        for i in range(4):
+            idx = (sel >> (4 * i)) & 0x7
+            out |= ((src >> (8 * idx)) & 0xFF) << (8 * i)
+        return out
+    a, b = 0x44332211, 0x88776655
+    assert prmt(a, b, 0x7531) == 0x88664422
