@@ -120,3 +120,33 @@ def test_graph_cache_keeps_eight(oracle_mod, torch_cuda):
             assert d.denoise(t, alpha, 1, 32) == k_ref
             assert d.stats()["graph"] == expect
             assert np.array_equal(t.cpu().numpy(), ref)
+
+
+def test_predicted_schedule_as_graph(oracle_mod, torch_cuda):
+    """The predicted-k schedule recorded as a graph and replayed: the graph
+    holds the predicted number of fused launches and then the list passes,
+    which continue exactly where the device's convergence state says; bytes
+    and k equal the oracle's for every call, and a repeated call replays."""
+    from paper_1306_5390_gb300 import hgrms
+    torch = torch_cuda
+    imgs = [noisy(r, c, dens, 8500 + i) for i, (r, c, dens) in enumerate([(333, 250, 0.3), (129, 700, 0.6)])]
+    refs = [oracle_mod.denoise(im, 10, 1, 32) for im in imgs]
+    srcs = [torch.from_numpy(im).cuda() for im in imgs]
+    ts = [torch.empty_like(s) for s in srcs]
+    with hgrms.Denoiser(0) as d:
+        try:
+            d.load_predictor(1)
+        except FileNotFoundError:
+            pytest.skip("no fitted predictor weights")
+        d.set_option(hgrms.HGRMS_OPT_PREDICT_K, 1)
+        d.set_option(hgrms.HGRMS_OPT_GRAPH, 1)
+        # (a call that grows the handle's buffers makes earlier graphs stale,
+        # so each image is recorded and then replayed)
+        for t, s, (ref, k_ref, _) in zip(ts, srcs, refs):
+            for rep in range(2):
+                t.copy_(s)
+                assert d.denoise(t, 10, 1, 32) == k_ref
+                st = d.stats()
+                assert st["k_pred"] >= 0, st
+                assert st["graph"] == (2 if rep == 0 else 1), st
+                assert np.array_equal(t.cpu().numpy(), ref)
