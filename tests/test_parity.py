@@ -309,3 +309,24 @@ def test_rms_arithmetic_exhaustive(torch_cuda):
             assert lib.hgrms_rms(s.data_ptr(), f.data_ptr(), out.data_ptr(), s.numel(), None) == 0
             expect = isq[(s.cpu().numpy() // flag)]
             assert np.array_equal(out.cpu().numpy(), expect), (flag, r)
+
+
+def _golden_files():
+    import os
+    d = os.path.join(os.path.dirname(__file__), "golden")
+    return sorted(f for f in os.listdir(d) if f.endswith(".txt"))
+
+
+@pytest.mark.parametrize("name", _golden_files())
+def test_golden_worked_examples_on_gpu(den, torch_cuda, name):
+    """The hand-derived worked examples (tests/golden, each citing its
+    passage of the paper) through the CUDA path: bytes, k and the converged
+    flag equal the values derived from the paper, with no oracle in
+    between."""
+    import os
+    from test_oracle import load_golden
+    g = load_golden(os.path.join(os.path.dirname(__file__), "golden", name))
+    for kernel in (0, 1):  # the default schedule and the unfused kernel
+        out, k, conv = gpu_denoise(den, torch_cuda, g["input"], g["alpha"], g["beta"], g["max_k"], kernel=kernel)
+        assert k == g["k"] and conv == bool(g["converged"]), (name, kernel, k, conv)
+        np.testing.assert_array_equal(out, g["output"], err_msg=f"{name} kernel {kernel}")
