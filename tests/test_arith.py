@@ -55,3 +55,25 @@ def test_gather_of_bytes_1_and_3():
         return out
     a, b = 0x44332211, 0x88776655
     assert prmt(a, b, 0x7531) == 0x88664422
+
+
+def test_two_stage_decision_table():
+    """beta 3's two-stage count: stage one keeps a pixel when its inner-ring
+    count K_in is 0 or 1 (flag bits: not settled, K_in == 1); stage two has
+    byte b = 4 K_out (+ 0..2) of its outer-ring count and calls it a
+    candidate when b < (4 if K_in == 1 else 8).  That must be K_in + K_out
+    <= 1 for every K_in <= 8 and K_out <= 40 (the 8 inner and 40 outer
+    neighbours of a 7 x 7 window)."""
+    for k_in in range(9):
+        unsettled = k_in <= 1
+        for k_out in range(41):
+            for k_other in range(41):  # the pair's other pixel only moves the carry
+                acc = (k_out * 0x3C00 + k_other * 0x3C00 * 65536) % 2**32
+                z = acc * 47 % 2**32
+                b_lo = (z >> 8) & 0xFF
+                cand = unsettled and b_lo < (4 if k_in == 1 else 8)
+                assert cand == (k_in + k_out <= 1), (k_in, k_out, k_other)
+                acc2 = (k_other * 0x3C00 + k_out * 0x3C00 * 65536) % 2**32
+                b_hi = (acc2 * 47 % 2**32) >> 24
+                cand_hi = unsettled and b_hi < (4 if k_in == 1 else 8)
+                assert cand_hi == (k_in + k_out <= 1), (k_in, k_out, k_other, "hi")
