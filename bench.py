@@ -61,12 +61,17 @@ def parse_args(argv=None):
     p.add_argument("--size", type=int, default=8192, help="side of the square image (8192 workload)")
     p.add_argument("--cpu-rows", type=int, default=128, help="rows of the oracle baseline sample")
     p.add_argument("--ref-rows", type=int, default=64, help="rows of each reference-arm step")
-    p.add_argument("--e2e-steps", type=int, default=3)
+    p.add_argument("--e2e-steps", type=int, default=10)
+    p.add_argument("--e2e-warmup", type=int, default=1)
+    p.add_argument("--fixed-k", type=int, default=5,
+                   help="also time the paper's fixed iteration factor (0 = skip)")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the 256x256 latency, 481x321 sweep and serving sections")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--batch-images", type=int, default=512,
                    help="images of the uneven-batch comparison (0 = skip it)")
     p.add_argument("--batch-steps", type=int, default=5)
-    p.add_argument("--loop-steps", type=int, default=2)
+    p.add_argument("--loop-steps", type=int, default=5)
     return p.parse_args(argv)
 
 
@@ -194,11 +199,10 @@ def run_ours(args, rank, world, local):
     ds = [hgrms.Denoiser(local, kernel=args.kernel, passes=args.passes, timing=True) for _ in betas]
     for dd in ds:
         dd.set_option(hgrms.HGRMS_OPT_GRAPH, args.graph)
-    d = ds[0]
 
-    def step(per_beta, ks):
+    def step(mk, ks):
         for i, b in enumerate(betas):
-            ds[i].denoise_async(work[i], alpha, b, max_k)
+            ds[i].denoise_async(work[i], alpha, b, mk)
         for i in range(len(betas)):
             ks[i] = ds[i].wait()
 
@@ -233,31 +237,38 @@ def run_ours(args, rank, world, local):
                         passes_executed=0, evals_fused=0, evals_list=0, ms_by_kind=[0.0, 0.0, 0.0],
                         n_by_kind=[0, 0, 0], T=0, ctas=0, calls=0) for b in betas}
 
-    ks = [0] * len(betas)
-    for _ in range(args.warmup):
-        fresh()
-        step(None, ks)
-        collect(new_acc(), ks)
-    acc = new_acc()
-    clocks = ClockSampler(local)
-    clocks.start()
-    total_ms = 0.0
-    units = 0
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    for _ in range(args.steps):
-        fresh()
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
-        ev0.record()
-        step(acc, ks)
-        ev1.record()
-        torch.cuda.synchronize()
-        collect(acc, ks)
-        total_ms += ev0.elapsed_time(ev1)
-        units += sum(rows * cols * acc[b]["k"] for b in betas)
-    clk = clocks.stop()
+
+    def timed_run(mk, steps, warm, clocks=None):
+        """warm untimed steps, then `steps` timed ones (CUDA events on the
+        stream the calls run on); returns (ms over the timed steps, pixel-
+        iterations, per-beta accumulators)."""
+        ks = [0] * len(betas)
+        for _ in range(warm):
+            fresh()
+            step(mk, ks)
+            collect(new_acc(), ks)
+        acc = new_acc()
+        if clocks:
+            clocks.start()
+        tot, units = 0.0, 0
+        for _ in range(steps):
+            fresh()
+            if dist is not None:
+                dist.barrier()
+            torch.cuda.synchronize()
+            ev0.record()
+            step(mk, ks)
+            ev1.record()
+            torch.cuda.synchronize()
+            collect(acc, ks)
+            tot += ev0.elapsed_time(ev1)
+            units += sum(rows * cols * acc[b]["k"] for b in betas)
+        clk = clocks.stop() if clocks else None
+        return tot, units, acc, clk
+
+    total_ms, units, acc, clk = timed_run(max_k, args.steps, args.warmup, ClockSampler(local))
     total_ms, units = combine_ranks(dist, "cuda", total_ms, units)
     value = units / (total_ms * 1e-3) / 1e6
 
@@ -266,79 +277,67 @@ def run_ours(args, rank, world, local):
     host_np = [p.numpy() for p in pinned]
     e2e_s = 0.0
     e2e_units = 0
-    for _ in range(args.e2e_steps):
+    for it in range(args.e2e_warmup + args.e2e_steps):
         for hn in host_np:
             hn[...] = w["noisy"]
+        flush.zero_()
+        torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
         t0 = time.perf_counter()
         for i, b in enumerate(betas):
             ds[i].denoise_async(pinned[i], alpha, b, max_k)
         ks = [ds[i].wait() for i in range(len(betas))]
-        e2e_s += time.perf_counter() - t0
-        e2e_units += sum(rows * cols * k for k in ks)
+        if it >= args.e2e_warmup:
+            e2e_s += time.perf_counter() - t0
+            e2e_units += sum(rows * cols * k for k in ks)
     e2e_s, e2e_units = combine_ranks(dist, "cuda", e2e_s, e2e_units)
     e2e_value = e2e_units / e2e_s / 1e6 if e2e_s > 0 else None
 
     peaks, peak_kind = measured_peaks()
+    hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     sm_mhz = float(peaks.get("sm_max_mhz", 2070.0))
     alu_peak = sms * 128 * sm_mhz * 1e6 / 1e9  # Gop/s: one 32-bit op per lane per clock
-    kind_name = {0: "fused_kernel", 1: "list_loop_kernel", 2: "plain_kernel"}
-    per_beta_out = {}
-    kernels = []  # (total ms, name, beta, tests, launches)
-    for b in betas:
-        a = acc[b]
-        taps = (2 * b + 1) ** 2 - 1
-        calls = max(1, a["calls"])
-        ev = {0: a["evals_fused"], 1: a["evals_list"], 2: a["passes_executed"] * rows * cols}
-        per_beta_out[str(b)] = dict(
-            k=a["k"], converged=bool(a["converged"]), passes_per_launch=a["T"],
-            work_launches_per_call=a["work_launches"] / calls,
-            kernel_ms_per_call=a["kernel_ms"] / calls,
-            idle_launch_ms_per_call=a["idle_kernel_ms"] / calls,
-            ms_per_call_by_kernel={kind_name[k]: a["ms_by_kind"][k] / calls for k in range(3) if a["n_by_kind"][k]},
-            launches_per_call_by_kernel={kind_name[k]: a["n_by_kind"][k] / calls for k in range(3)
-                                         if a["n_by_kind"][k]},
-            pixel_evals_per_call={kind_name[k]: ev[k] / calls for k in range(3) if a["n_by_kind"][k]},
-            mpix_iter_per_s=rows * cols * a["k"] * a["calls"] / (a["kernel_ms"] * 1e-3) / 1e6
-            if a["kernel_ms"] > 0 else None)
-        for k in range(3):
-            if a["n_by_kind"][k]:
-                kernels.append((a["ms_by_kind"][k], kind_name[k], b, ev[k] * taps, a["n_by_kind"][k], a["T"]))
-    kernels.sort(reverse=True)
-    dom_ms, dom_name, dom_b, dom_tests, dom_n, dom_T = kernels[0]
-    launch_s = dom_ms * 1e-3 / dom_n
-    achieved = dom_tests / dom_n / launch_s / 1e9
-    tname = f"{dom_name}<beta={dom_b},T={dom_T}>" if dom_name == "fused_kernel" else f"{dom_name}<beta={dom_b}>"
+    per_beta_out, kernels = per_kernel(acc, betas, rows, cols)
+    dom = kernels[0]
+    launch_s = dom["ms"] * 1e-3 / dom["n"]
+    taps = (2 * dom["beta"] + 1) ** 2 - 1
+    dense_units = dom["passes"] / dom["n"] * rows * cols * taps      # every pixel of every pass of one launch
+    eval_units = dom["evals"] / dom["n"] * taps                       # only the pixels the launch evaluated
+    achieved = dense_units / launch_s / 1e9
     roofline = {
         "bound": "alu",
-        "kernel": tname,
+        "kernel": dom["name"],
         "achieved": round(achieved, 1),
         "peak": round(alu_peak, 1),
         "unit": "Gop/s",
         "frac": round(achieved / alu_peak, 4),
-        "traffic": traffic_from_profiles(dom_name, dom_b, dom_T, rows, cols),
-        "hbm_achieved_frac": None,
-        "algorithmic_unit": (f"one neighbour comparison of Algorithms 1-2 ({(2 * dom_b + 1) ** 2 - 1} per evaluated "
-                             "pixel), counting the pixels a pass must evaluate: every pixel in a dense pass, the "
-                             "pixels within beta of a previous-pass change otherwise"),
+        "traffic": traffic_from_profiles(dom["kind"], dom["beta"], dom["T"], rows, cols),
+        "algorithmic_unit": (f"one neighbour comparison of Algorithms 1-2, {taps} per pixel per pass, counted for "
+                             "every pixel of every pass the launch runs"),
+        "passes_per_launch": round(dom["passes"] / dom["n"], 3),
         "peak_basis": f"{sms} SMs x 128 lanes x {sm_mhz:.0f} MHz ({peak_kind} sm_max_mhz)",
         "launch_ms": round(launch_s * 1e3, 4),
-        "share_of_step": round(dom_ms / max(1e-9, total_ms), 4),
+        "share_of_step": round(dom["ms"] / max(1e-9, total_ms), 4),
+        "evaluated_frac": round(eval_units / launch_s / 1e9 / alu_peak, 4),
+        "evaluated_basis": "the same comparisons counted only for the pixels the launch evaluated (every pixel of "
+                           "a dense pass, the pixels within beta of a change of the previous pass otherwise)",
+        "hbm_effective_frac": round(2.0 * dom["passes"] / dom["n"] * rows * cols / launch_s / 1e9 / hbm_peak, 4),
+        "hbm_effective_basis": f"2 B per pixel per pass over the launch time, of {hbm_peak:.0f} GB/s {peak_kind}",
+        "hbm_achieved_frac": None,
     }
     if roofline["traffic"]:
         # DRAM bytes the kernel moves (ncu) over its measured launch time.
-        roofline["hbm_achieved_frac"] = round(roofline["traffic"] / launch_s / 1e9 / peaks.get("hbm_gbs", 6800.0), 4)
+        roofline["hbm_achieved_frac"] = round(roofline["traffic"] / launch_s / 1e9 / hbm_peak, 4)
     # Share of issue slots the kernel used (ncu smsp__issue_active of the same
-    # summary): the comparisons it does per issued instruction, not idle
-    # hardware, are what the ALU fraction above reflects.
-    roofline["issue_active_frac"] = profile_metric(dom_name, dom_b, dom_T, rows, cols,
+    # summary of the current sources).
+    roofline["issue_active_frac"] = profile_metric(dom["kind"], dom["beta"], dom["T"], rows, cols,
                                                    "smsp__issue_active.avg.pct_of_peak_sustained_active", 0.01)
     pix_iters_per_step = units / max(1, args.steps) / world
     step_s = total_ms * 1e-3 / args.steps
     hbm_eff = 2.0 * pix_iters_per_step / step_s / 1e9
-    launches = sum(acc[b]["launches"] + 3 * acc[b]["calls"] for b in betas)  # + copy-in, init, copy-out
+    launches = sum(acc[b]["launches"] + 3 * acc[b]["calls"] for b in betas)  # + init, tile map, copy-out
 
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
@@ -352,28 +351,184 @@ def run_ours(args, rank, world, local):
                        args.kernel], "rows": rows, "cols": cols},
         "roofline": roofline,
         "hbm_effective": {"bytes_per_pixel_iter": 2, "achieved_gbs": round(hbm_eff, 1),
-                          "peak_gbs": peaks.get("hbm_gbs"), "frac": round(hbm_eff / peaks.get("hbm_gbs", 6800.0), 4),
-                          "peak_kind": peak_kind},
+                          "peak_gbs": hbm_peak, "frac": round(hbm_eff / hbm_peak, 4), "peak_kind": peak_kind},
         "per_beta": per_beta_out,
         "e2e": {"value": round(e2e_value, 1) if e2e_value else None, "unit": UNIT,
                 "h2d_bytes_per_step": rows * cols * len(betas), "d2h_bytes_per_step": rows * cols * len(betas),
-                "steps": args.e2e_steps, "timer": "host perf_counter around the C-ABI calls on pinned host images"},
+                "steps": args.e2e_steps, "warmup": args.e2e_warmup,
+                "timer": "host perf_counter around the C-ABI calls on pinned host images"},
         "gpu_launches": launches,
         "clocks": clk,
     }
+    if args.fixed_k > 0 and args.fixed_k != max_k:
+        out[f"fixed_k{args.fixed_k}"] = fixed_k_section(timed_run, args, betas, rows, cols, hbm_peak, peak_kind)
+    for dd in ds:
+        dd.close()
+    del work, pinned, host_np
+    torch.cuda.empty_cache()
+    if not args.no_extras:
+        out["latency_256"] = latency_section(torch, local)
+        out["bsds_sweep"] = bsds_section(torch, local)
     if args.batch_images > 0:
         out["batched"] = batch_section(torch, local, args)
         launches_b = out["batched"].pop("_launches")
         out["gpu_launches_batched_step"] = launches_b
+    if not args.no_extras and args.serve_seconds > 0 and world == 1:
+        out["serve"] = serve_section(args, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(w, args.cpu_rows)
-    for dd in ds:
-        dd.close()
     if dist is not None:
         dist.barrier()
         dist.destroy_process_group()
     if rank == 0:
         print(json.dumps(out), flush=True)
+
+
+KIND_NAME = {0: "fused_kernel", 1: "list_loop_kernel", 2: "plain_kernel"}
+
+
+def per_kernel(acc, betas, rows, cols):
+    """Per-beta summary and the per-kernel list (largest device time first)
+    from the accumulated statistics of the timed calls.  A kernel's passes
+    are the passes its launches ran: the fused launches ran T passes each
+    (the last capped by what was left), the list-pass launch the rest."""
+    per_beta_out = {}
+    kernels = []
+    for b in betas:
+        a = acc[b]
+        calls = max(1, a["calls"])
+        nf = a["n_by_kind"][0]
+        fused_passes = min(a["passes_executed"], nf * a["T"])
+        passes = {0: fused_passes, 1: a["passes_executed"] - fused_passes, 2: a["passes_executed"]}
+        ev = {0: a["evals_fused"], 1: a["evals_list"], 2: a["passes_executed"] * rows * cols}
+        per_beta_out[str(b)] = dict(
+            k=a["k"], converged=bool(a["converged"]), passes_per_launch=a["T"],
+            work_launches_per_call=a["work_launches"] / calls,
+            kernel_ms_per_call=a["kernel_ms"] / calls,
+            idle_launch_ms_per_call=a["idle_kernel_ms"] / calls,
+            ms_per_call_by_kernel={KIND_NAME[k]: a["ms_by_kind"][k] / calls for k in range(3) if a["n_by_kind"][k]},
+            launches_per_call_by_kernel={KIND_NAME[k]: a["n_by_kind"][k] / calls for k in range(3)
+                                         if a["n_by_kind"][k]},
+            passes_per_call_by_kernel={KIND_NAME[k]: passes[k] / calls for k in range(3) if a["n_by_kind"][k]},
+            pixel_evals_per_call={KIND_NAME[k]: ev[k] / calls for k in range(3) if a["n_by_kind"][k]},
+            mpix_iter_per_s=rows * cols * a["k"] * a["calls"] / (a["kernel_ms"] * 1e-3) / 1e6
+            if a["kernel_ms"] > 0 else None)
+        for k in range(3):
+            if a["n_by_kind"][k]:
+                name = (f"{KIND_NAME[k]}<beta={b},T={a['T']}>" if k == 0 else f"{KIND_NAME[k]}<beta={b}>")
+                kernels.append(dict(ms=a["ms_by_kind"][k], name=name, kind=KIND_NAME[k], beta=b,
+                                    n=a["n_by_kind"][k], T=a["T"], passes=passes[k], evals=ev[k]))
+    kernels.sort(key=lambda x: -x["ms"])
+    return per_beta_out, kernels
+
+
+def fixed_k_section(timed_run, args, betas, rows, cols, hbm_peak, peak_kind):
+    """The paper's fixed iteration factor (k = 5, no convergence before it on
+    this workload) on the same image and handles: the densest passes, where
+    the fused tile kernel does nearly all the work."""
+    mk = args.fixed_k
+    steps = max(3, args.steps // 2)
+    tot, units, acc, _ = timed_run(mk, steps, max(3, args.warmup // 2))
+    per_beta_out, kernels = per_kernel(acc, betas, rows, cols)
+    step_s = tot * 1e-3 / steps
+    res = {"max_k": mk, "steps": steps, "ms_per_step": round(tot / steps, 4),
+           "value": round(units / (tot * 1e-3) / 1e6, 1), "unit": UNIT,
+           "hbm_effective_frac": round(2.0 * units / steps / step_s / 1e9 / hbm_peak, 4),
+           "hbm_effective_basis": f"2 B per pixel-iteration over the step time, of {hbm_peak:.0f} GB/s {peak_kind}",
+           "per_beta": {}}
+    for b in betas:
+        a = acc[b]
+        calls = max(1, a["calls"])
+        fused_ms = a["ms_by_kind"][0] / calls
+        res["per_beta"][str(b)] = {
+            "k": a["k"], "kernel_ms_per_call": round(a["kernel_ms"] / calls, 4),
+            "fused_ms_per_call": round(fused_ms, 4),
+            "fused_hbm_effective_frac": round(2.0 * rows * cols * a["k"] / (fused_ms * 1e-3) / 1e9 / hbm_peak, 4)
+            if fused_ms > 0 else None,
+            "ms_per_call_by_kernel": per_beta_out[str(b)]["ms_per_call_by_kernel"]}
+    return res
+
+
+def latency_section(torch, local, calls=200):
+    """One 256 x 256 image (10 % impulse noise, alpha 10, beta 1, max_k 32),
+    device-resident: host-timed synchronous hgrms_denoise calls (the call's
+    whole latency, including its one read of k), median and p90 over calls
+    after warm-up."""
+    from paper_1306_5390_gb300 import hgrms, synth
+    w = synth.workload_256()
+    src = torch.from_numpy(w["noisy"]).cuda()
+    t = torch.empty_like(src)
+    lat = []
+    k = None
+    with hgrms.Denoiser(local) as d:
+        for i in range(calls + 20):
+            t.copy_(src)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            k = d.denoise(t, w["alpha"], w["beta"], w["max_k"])
+            dt = time.perf_counter() - t0
+            if i >= 20:
+                lat.append(dt * 1e6)
+    lat = np.array(lat)
+    return {"workload": "256x256 uint8, 10% salt-and-pepper, alpha 10, beta 1, max_k 32, device-resident",
+            "k": k, "us_per_call_p50": round(float(np.median(lat)), 2),
+            "us_per_call_p90": round(float(np.percentile(lat, 90)), 2), "calls": calls,
+            "mpix_iter_per_s": round(256 * 256 * k / (np.median(lat) * 1e-6) / 1e6, 1),
+            "timer": "host perf_counter around the synchronous C-ABI call"}
+
+
+def psnr(ref, img):
+    mse = float(np.mean((ref.astype(np.float64) - img.astype(np.float64)) ** 2))
+    return float("inf") if mse == 0 else 10.0 * math.log10(255.0 ** 2 / mse)
+
+
+def bsds_section(torch, local, n_images=64, reps=3):
+    """The 481x321 / 321x481 sweep (64 images with texture and +/-8 uniform
+    noise; impulse density 10..90 %, alpha 5/10/20, beta 1/2; max_k 32): for
+    each of the 30 settings, the 64 images in one device-resident
+    hgrms_denoise_batch call (CUDA events, median of `reps`), the time per
+    iteration (the batch runs as many passes as its largest k, plus the pass
+    that finds no change), and the mean PSNR of the noisy and the denoised
+    images against the clean ones (the quality measure of the paper's
+    Table 2, on these stand-in images)."""
+    from paper_1306_5390_gb300 import hgrms, synth
+    settings = {}
+    for wi in synth.workload_bsds_like(n_images):
+        key = (wi["density"], wi["alpha"], wi["beta"])
+        settings.setdefault(key, []).append(wi)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    rows_out = []
+    with hgrms.Denoiser(local) as d:
+        for (dens, a, b), items in sorted(settings.items()):
+            pristine = [torch.from_numpy(x["noisy"]).cuda() for x in items]
+            work = [p.clone() for p in pristine]
+            times = []
+            ks = None
+            for r in range(reps + 1):
+                for t, p in zip(work, pristine):
+                    t.copy_(p)
+                torch.cuda.synchronize()
+                ev0.record()
+                ks = d.denoise_batch(work, a, b, 32)
+                ev1.record()
+                torch.cuda.synchronize()
+                if r:
+                    times.append(ev0.elapsed_time(ev1))
+            ms = float(np.median(times))
+            outs = [t.cpu().numpy() for t in work]
+            p_noisy = float(np.mean([psnr(x["clean"], x["noisy"]) for x in items]))
+            p_out = float(np.mean([psnr(x["clean"], o) for x, o in zip(items, outs)]))
+            passes = max(ks) + (1 if max(ks) < 32 else 0)
+            px_iters = sum(x["noisy"].size * k for x, k in zip(items, ks))
+            rows_out.append({"density": dens, "alpha": a, "beta": b, "k_mean": round(float(np.mean(ks)), 2),
+                             "k_max": int(max(ks)), "ms_per_batch": round(ms, 4),
+                             "ms_per_iteration": round(ms / max(1, passes), 5),
+                             "mpix_iter_per_s": round(px_iters / (ms * 1e-3) / 1e6, 1),
+                             "psnr_noisy_db": round(p_noisy, 2), "psnr_denoised_db": round(p_out, 2)})
+    return {"workload": f"{n_images} uint8 images 481x321 / 321x481 (texture, +/-8 uniform noise), salt-and-pepper "
+                        "10..90%, alpha 5/10/20, beta 1/2, max_k 32; one batch of the 64 images per setting",
+            "settings": rows_out}
 
 
 def kernel_source_hash():
@@ -482,7 +637,7 @@ def batch_section(torch, local, args):
     }
 
 
-def run_serve(args, rank, world, local):
+def serve_section(args, local):
     """Serving: a Poisson stream of denoising requests (square images with
     sides log-uniform in 256..4096, impulse density 5..80 %, alpha 10, beta 1
     or 2, max_k 32), each on its own device buffer, through the request
@@ -491,9 +646,7 @@ def run_serve(args, rank, world, local):
     -> result ready)."""
     import threading
     import torch
-    from paper_1306_5390_gb300 import build, hgrms, synth
-    build.build()
-    torch.cuda.set_device(local)
+    from paper_1306_5390_gb300 import hgrms, synth
     rng = np.random.Generator(np.random.PCG64(synth.seed_for(4, 0)))
     pool = []
     for i in range(48):
@@ -583,27 +736,42 @@ def run_serve(args, rank, world, local):
     srv.close()
     wall = t_end - t0
     lat_a = np.array(lat)
-    out = {
-        "metric": "images/s served (continuous batching, bit-exact per request)",
-        "value": round(n_req / wall, 1), "unit": "images/s", "n_gpus": 1, "steps": n_req, "warmup": 2 * len(pool),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
-        "data": "synthetic (seeded Gaussian-bump + gradient content, salt-and-pepper noise)",
-        "config": {"workload": ((f"Poisson {args.serve_rate:.0f} req/s for {args.serve_seconds:.1f} s"
-                                 if args.serve_rate > 0 else f"{n_req} requests without pacing") + ", square images "
-                                "256..4096 (log-uniform, 48 seeded images), salt-and-pepper 5..80%, alpha 10, "
-                                "beta 1 or 2, max_k 32, device-resident"),
-                   "slots": args.serve_slots, "hbm_budget_gb": args.serve_budget_gb},
+    return {
+        "workload": ((f"Poisson {args.serve_rate:.0f} req/s for {args.serve_seconds:.1f} s"
+                      if args.serve_rate > 0 else f"{n_req} requests without pacing") + ", square images "
+                     "256..4096 (log-uniform, 48 seeded images), salt-and-pepper 5..80%, alpha 10, "
+                     "beta 1 or 2, max_k 32, device-resident"),
+        "slots": args.serve_slots, "hbm_budget_gb": args.serve_budget_gb,
+        "requests": n_req, "warmup_requests": 2 * len(pool),
+        "images_per_s": round(n_req / wall, 1),
         "latency_ms": {"p50": round(float(np.percentile(lat_a, 50)), 3),
                        "p90": round(float(np.percentile(lat_a, 90)), 3),
                        "p99": round(float(np.percentile(lat_a, 99)), 3),
                        "max": round(float(lat_a.max()), 3),
                        "queue_p50": round(float(np.percentile(queue_ms, 50)), 3)},
         "offered_rate": args.serve_rate,
-        "achieved_rate": round(n_req / wall, 1),
         "submit_seconds": round(t_submitted - t0, 3),
         "mpix_iter_per_s": round(px_iters[0] / wall / 1e6, 1),
         "batches": st["batches"], "mean_batch": round(float(np.mean(bsz)), 2),
         "max_in_flight": st["max_in_flight"], "errors": st["error"],
+        "timer": "host perf_counter from the first submit to the last result; latency from the server",
+    }
+
+
+def run_serve(args, rank, world, local):
+    """``--workload serve``: the serving section alone, as the JSON line."""
+    import torch
+    from paper_1306_5390_gb300 import build
+    build.build()
+    torch.cuda.set_device(local)
+    sv = serve_section(args, local)
+    out = {
+        "metric": "images/s served (continuous batching, bit-exact per request)",
+        "value": sv["images_per_s"], "unit": "images/s", "n_gpus": 1, "steps": sv["requests"],
+        "warmup": sv["warmup_requests"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "u8", "data": "synthetic (seeded Gaussian-bump + gradient content, salt-and-pepper noise)",
+        "config": {"workload": sv["workload"], "slots": sv["slots"], "hbm_budget_gb": sv["hbm_budget_gb"]},
+        **{k: v for k, v in sv.items() if k not in ("workload", "slots", "hbm_budget_gb")},
     }
     if rank == 0:
         print(json.dumps(out), flush=True)

@@ -62,13 +62,18 @@ typedef struct hgrms_ctx* hgrms_t;
 
 /* Create a handle on CUDA device `device`.  `cuda_stream` is a cudaStream_t
  * to issue work on, or NULL for the device's default (legacy) stream.  The
- * handle owns its device buffers (two padded image canvases and a small
- * control block) and reuses them across calls, growing them on demand.
+ * handle owns its device buffers and reuses them across calls, growing them on
+ * demand: the image buffers that stand for I and the temporary image I' of
+ * Section 2 (three padded canvases, so a pass never copies I' back), the
+ * change lists and bitmaps that carry the pixels a pass changed to the next
+ * pass, and the control block holding the Section 2 iteration state (k, the
+ * converged flag, max_k).
  * Writes the handle to *out and returns HGRMS_OK, or a negative code (and
  * *out = NULL). */
 int hgrms_create(hgrms_t* out, int device, void* cuda_stream);
 
-/* Release the handle and everything it owns.  NULL is accepted. */
+/* Release the handle and everything it owns (the buffers above; the
+ * iteration state of Section 2 dies with it).  NULL is accepted. */
 void hgrms_destroy(hgrms_t h);
 
 /* Denoise one image in place (the full method above).
@@ -80,7 +85,9 @@ int hgrms_denoise(hgrms_t h, uint8_t* img, int rows, int cols,
                   int alpha, int beta, int max_k);
 
 /* Denoise n independent images with the same alpha, beta and max_k, in
- * place.  imgs[i] has rows[i] x cols[i] pixels (each device memory or host
+ * place: Section 2's iteration of Algorithms 1-2 run on each image, with the
+ * stop rule applied per image (image i stops contributing passes once one of
+ * its passes changes nothing, or at k_i = max_k).  imgs[i] has rows[i] x cols[i] pixels (each device memory or host
  * memory, as for hgrms_denoise).  k_out[i] receives image i's k, exactly what
  * hgrms_denoise returns for that image alone; image i converged (a further
  * pass would change nothing) exactly when k_out[i] < max_k.  With the
@@ -118,9 +125,11 @@ int hgrms_denoise_async(hgrms_t h, uint8_t* img, int rows, int cols,
  * outstanding. */
 int hgrms_wait(hgrms_t h);
 
-/* 1 if the last hgrms_denoise ended because a pass changed no pixel (the
- * image is a fixed point), 0 if it stopped at max_k, negative on a bad
- * handle. */
+/* The stop rule of Section 2 ("until no noise remains", capped by the
+ * iteration factor): 1 if the last hgrms_denoise ended because a pass changed
+ * no pixel (the image is a fixed point), 0 if it stopped at max_k, negative
+ * on a bad handle.  After hgrms_denoise_batch: 1 only if every image
+ * converged. */
 int hgrms_converged(hgrms_t h);
 
 /* Human-readable text for a return code (static storage). */
@@ -161,13 +170,20 @@ int hgrms_rms(const int* sum, const int* flag, int* out, int n, void* cuda_strea
  * Returns k (as hgrms_denoise) or a negative code; HGRMS_ETOOBIG when the
  * scratch the image needs exceeds the array (images with rows, cols <= 2048
  * always fit; larger ones fit while their two padded canvases and change
- * bitmaps do).  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) and may load the library's device code:
- * make that first call before capturing any stream into a CUDA graph.  All
- * calls on a device share the array (it keeps the last call's contents;
- * each call re-initialises what it reads), so calls whose GPU work overlaps
- * - from two streams or two host threads - race and must be serialised by
- * the caller. */
+ * bitmaps do).  There is no handle, so there is no hgrms_converged for this
+ * call: a return of k < max_k means it converged (a pass changed nothing),
+ * while k == max_k does not tell whether pass max_k happened to leave a fixed
+ * point.  The fused launches are queued in groups of 32 passes; after each
+ * group (when more are due) the call reads k and the converged flag from the
+ * device and stops once it has converged, so a large max_k costs nothing
+ * after convergence beyond the group it falls in.  Every call looks up the
+ * array's address on the current device (cudaGetSymbolAddress, which
+ * allocates nothing); the first call on a device may also load the
+ * library's device code there, so make that first call before capturing any
+ * stream into a CUDA graph.  All calls on a device share the array (it
+ * keeps the last call's contents; each call re-initialises what it reads),
+ * so calls whose GPU work overlaps - from two streams or two host threads -
+ * race and must be serialised by the caller. */
 int hgrms_denoise_noalloc(uint8_t* img, int rows, int cols, int alpha, int beta, int max_k,
                           void* cuda_stream);
 

@@ -12,10 +12,12 @@
 //
 // The array is part of the library's device image: every GPU on which the
 // library is loaded holds it until the process exits.  Host code cannot use
-// the array's name as a device address, so the first call on each device
-// asks the runtime for the address (cudaGetSymbolAddress, with that device
-// current) and caches it.
-#include <mutex>
+// the array's name as a device address, so every call asks the runtime for
+// the address on the current device (cudaGetSymbolAddress, which allocates
+// nothing).  The first call on a device also loads the library's device code
+// there; later calls only look the address up, so a context that was reset
+// and rebuilt never sees an address from before the reset.
+#include <cstddef>
 
 #include "../../include/hgrms.h"
 #include "fused.cuh"
@@ -26,22 +28,21 @@ namespace {
 constexpr size_t kScratchBytes = (size_t)HGRMS_NOALLOC_SCRATCH_BYTES;
 __device__ __align__(256) uint8_t g_noalloc_scratch[kScratchBytes];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-uint8_t* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the array on `device` (current), looked up once.
-cudaError_t scratch_address(int device, uint8_t** out) {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_addr[device]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess) return e;
-        g_scratch_addr[device] = static_cast<uint8_t*>(p);
-    }
-    *out = g_scratch_addr[device];
+// Device address of the array on the current device.
+cudaError_t scratch_address(uint8_t** out) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    *out = static_cast<uint8_t*>(p);
     return cudaSuccess;
 }
+
+static_assert(offsetof(hg::Ctrl, k) == 0 && offsetof(hg::Ctrl, converged) == sizeof(unsigned),
+              "the group check reads k and converged as two leading words");
+
+// Fused launches queued before the host checks whether the call has
+// converged: enough for 32 passes (one group for the usual max_k <= 32).
+int launches_per_check(int T) { return (32 + T - 1) / T; }
 
 size_t align256(size_t n) { return (n + 255) / 256 * 256; }
 
@@ -65,7 +66,6 @@ extern "C" __attribute__((visibility("default"))) int hgrms_denoise_noalloc(uint
         return HGRMS_EINVAL;
     int device = 0;
     HG_NA_TRY(cudaGetDevice(&device));
-    if (device < 0 || device >= kMaxDevices) return HGRMS_ENODEV;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, img) != cudaSuccess) {
         cudaGetLastError();
@@ -90,7 +90,7 @@ extern "C" __attribute__((visibility("default"))) int hgrms_denoise_noalloc(uint
     if (need > kScratchBytes) return HGRMS_ETOOBIG;
 
     uint8_t* base = nullptr;
-    HG_NA_TRY(scratch_address(device, &base));
+    HG_NA_TRY(scratch_address(&base));
     cudaStream_t s = (cudaStream_t)cuda_stream;
     int sms = 0;
     HG_NA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
@@ -136,8 +136,22 @@ extern "C" __attribute__((visibility("default"))) int hgrms_denoise_noalloc(uint
     HG_NA_TRY(hg::launch_copy_in(img, rows, cols, a.canvas[0], pitch, sms, s));
     HG_NA_TRY(hg::launch_ctrl_init(ctrl, (unsigned)max_k, s));
     HG_NA_TRY(cudaMemsetAsync(a.chg_maps, 0, map_bytes, s));
+    // Launches after the call has converged return at once but still cost a
+    // wave each, so they are queued in groups, and between groups the host
+    // reads k and the converged flag (into stack memory) and stops early.
     const int launches = (max_k + T - 1) / T;
-    for (int i = 0; i < launches; ++i) HG_NA_TRY(fe->launch(a, tiles_x * tiles_y, s));
+    const int group = launches_per_check(T);
+    for (int done = 0; done < launches;) {
+        const int n = launches - done < group ? launches - done : group;
+        for (int i = 0; i < n; ++i) HG_NA_TRY(fe->launch(a, tiles_x * tiles_y, s));
+        done += n;
+        if (done < launches) {
+            unsigned st[2] = {0u, 0u};  // Ctrl::k, Ctrl::converged
+            HG_NA_TRY(cudaMemcpyAsync(st, ctrl, sizeof(st), cudaMemcpyDeviceToHost, s));
+            HG_NA_TRY(cudaStreamSynchronize(s));
+            if (st[1] || st[0] >= (unsigned)max_k) break;
+        }
+    }
     HG_NA_TRY(hg::launch_copy_out(ctrl, a.canvas, pitch, img, rows, cols, sms, s));
     unsigned k = 0;
     HG_NA_TRY(cudaMemcpyAsync(&k, &ctrl->k, sizeof(k), cudaMemcpyDeviceToHost, s));

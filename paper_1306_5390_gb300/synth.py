@@ -163,13 +163,14 @@ def workload_256():
                 alpha=10, beta=1, max_k=32, seed=seed)
 
 
-def workload_bsds_like(n_images: int = 64):
+def workload_bsds_like(n_images: int = 64, first: int = 0, last: int = None):
     """64 images, half 481 x 321 and half 321 x 481 (the BSDS shapes), with
     texture and +/-8 uniform noise; swept over impulse density
     {10,30,50,70,90} %, alpha {5,10,20} and beta {1,2}.  Yields one dict per
-    (image, setting)."""
+    (image, setting), for images first .. last - 1 (default all; each image
+    comes from its own seed, so a slice holds the same images as the whole)."""
     dens = (0.10, 0.30, 0.50, 0.70, 0.90)
-    for i in range(n_images):
+    for i in range(first, n_images if last is None else min(last, n_images)):
         rows, cols = (321, 481) if i % 2 == 0 else (481, 321)
         seed = seed_for(1, i)
         clean = clean_image(rows, cols, seed, texture=True, uniform_noise=8)

@@ -6,8 +6,8 @@ computes for that image alone (integer arithmetic: tolerance zero), and
 image i converged exactly when k_i < max_k.  Covers uneven sizes with
 degenerate images in the same batch, every beta with a compiled default
 kernel, alpha and max_k edge values, chunking by memory budget and by the
-32-bit change-list packing, list overflow, host pointers, and a slice of the
-uneven 128..2048 workload at full size.
+32-bit change-list packing, list overflow, host pointers, and all 512 images of the uneven
+128..2048 workload at full size.
 """
 import numpy as np
 import pytest
@@ -180,12 +180,47 @@ def test_batch_equals_single_calls(den, torch_cuda):
         assert np.array_equal(t.cpu().numpy(), out)
 
 
-def test_uneven_workload_slice_full_size(oracle_mod, den, torch_cuda):
-    """Six images of the uneven 128..2048 workload (its own sizes and
-    densities), batched, against the oracle."""
-    imgs = [w["noisy"] for w in synth.workload_batch(512, first=0, last=6)]
-    outs, ks, conv = run_batch(den, torch_cuda, imgs, 10, 1, 32)
-    check(oracle_mod, imgs, outs, ks, conv, 10, 1, 32, "uneven")
+def test_uneven_workload_all_512_images(oracle_mod, torch_cuda):
+    """The whole uneven workload (512 images, sides uniform in 128..2048,
+    density 5..70 %, 629 M pixels) as the benchmark runs it: the images one
+    after another in one device buffer, one hgrms_denoise_batch call on an
+    autotuned handle (the first call tunes, the second reuses the choice),
+    and with the learned k-predictor choosing the schedule.  Every image's
+    bytes, k and converged flag (k < max_k) against the oracle, which runs
+    image by image on all host cores."""
+    import oracle_pool
+    from paper_1306_5390_gb300 import hgrms
+    torch = torch_cuda
+    n = 512
+    res = oracle_pool.batch_denoise(n)
+    shapes = [r[0].shape for r in res]
+    sizes = [a * b for a, b in shapes]
+    offs = np.cumsum([0] + sizes)
+    pristine = torch.from_numpy(np.concatenate([r[0].ravel() for r in res])).cuda()
+    work = torch.empty_like(pristine)
+    views = [work[int(offs[i]):int(offs[i + 1])].view(shapes[i]) for i in range(n)]
+    d = hgrms.Denoiser(0, autotune=True)
+    try:
+        runs = []
+        for call in range(2):
+            work.copy_(pristine)
+            runs.append((d.denoise_batch(views, 10, 1, 32), work.cpu().numpy()))
+        try:
+            d.load_predictor(1)
+            d.set_option(hgrms.HGRMS_OPT_PREDICT_K, 1)
+            work.copy_(pristine)
+            runs.append((d.denoise_batch(views, 10, 1, 32), work.cpu().numpy()))
+        except FileNotFoundError:
+            pass
+    finally:
+        d.close()
+    for ri, (ks, flat) in enumerate(runs):
+        bad = []
+        for i, (noisy, ref, k_ref, c_ref) in enumerate(res):
+            out = flat[int(offs[i]):int(offs[i + 1])].reshape(shapes[i])
+            if k_ref != ks[i] or c_ref != (ks[i] < 32) or not np.array_equal(out, ref):
+                bad.append((i, shapes[i], ks[i], k_ref, int((out != ref).sum())))
+        assert not bad, f"run {ri}: {len(bad)} images differ, first {bad[:5]}"
 
 
 @pytest.mark.parametrize("beta,passes,max_k,list_cap", [(1, 0, 32, 0), (1, 3, 32, 0), (2, 0, 32, 0), (3, 0, 13, 0),
