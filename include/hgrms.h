@@ -336,6 +336,13 @@ int hgrms_predictor_grad(hgrms_t h, const float* weights, const float* x0, const
                                      else as a dense pass (0 = built-in: 2048 for beta 2, else
                                      4096) */
 
+#define HGRMS_OPT_WAIT_TEST 12 /* for tests of the bounded device wait (not for production): N > 0 makes
+                                   every grid barrier of the list-pass launch wait for one arrival more
+                                   than the launch has CTAs - an arrival that never comes - and give up
+                                   after N polls (at most 2^22); the call then returns HGRMS_ETIMEOUT once
+                                   a list pass runs, its image unspecified, and the handle stays usable.
+                                   0 = off (default) */
+
 /* Set an option.  Returns HGRMS_OK or HGRMS_EINVAL (unknown option or value,
  * e.g. a pass count that has no compiled kernel for some beta is rejected at
  * denoise time with HGRMS_EINVAL). */

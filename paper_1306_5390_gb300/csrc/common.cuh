@@ -152,6 +152,12 @@ struct PassArgs {
     // image, ImgDesc::user for a batch; null = read the canvas.
     const uint8_t* user0;
     int list_ctas;            // list-pass loop CTAs (0 = as many as can be co-resident)
+    // Test of the bounded barrier wait (HGRMS_OPT_WAIT_TEST): every grid
+    // barrier of the list-pass loop waits for bar_extra arrivals more than
+    // the launch has CTAs, and gives up after bar_spins polls (0 = the
+    // built-in limit of one to two seconds).
+    unsigned bar_extra = 0;
+    unsigned bar_spins = 0;
 };
 
 // floor(sqrt(floor(sum / flag))) exactly (the root mean square of Algorithm
@@ -166,6 +172,29 @@ struct PassArgs {
 __device__ __forceinline__ int rms_floor(float sum, int flag) {
     const float q = floorf(__fdiv_rn(sum, (float)flag));
     return (int)floorf(__fsqrt_rn(q));
+}
+
+// floor(sqrt(q)) for 0 <= q <= 65025.  rsqrtf is within 2 ulp, so q * rsqrtf(q)
+// is within 10^-4 of sqrt(q) and its nearest integer is floor(sqrt(q)) or one
+// more; r * r > q removes the excess.  q = 0 takes rsqrtf(1), so the product
+// is 0.
+__device__ __forceinline__ int isqrt_u16(int q) {
+    const float qf = (float)q;
+    int r = __float2int_rn(qf * rsqrtf(fmaxf(qf, 1.f)));
+    r -= (r * r > q) ? 1 : 0;
+    return r;
+}
+
+// The root mean square of a replaced pixel of a 3 x 3 window (beta 1): the
+// test flag > pix_count - 3 = 6 leaves flag in {7, 8, 9}, so floor(sum /
+// flag) is the high word of sum * ceil(2^32 / flag) - division by an
+// invariant integer through multiplication (Granlund and Montgomery, 1994),
+// exact here because sum <= 9 * 255^2 is far below 2^32 / (flag *
+// ceil(2^32 / flag) - 2^32).  Checked for every sum and flag through
+// hgrms_rms.
+__device__ __forceinline__ int rms_floor_3x3(int sum, int flag) {
+    const unsigned m = flag == 7 ? 0x24924925u : (flag == 8 ? 0x20000000u : 0x1C71C71Du);
+    return isqrt_u16((int)__umulhi((unsigned)sum, m));
 }
 
 // Passes the launch must run: 0 when the call has finished.

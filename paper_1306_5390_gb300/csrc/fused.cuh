@@ -244,28 +244,71 @@ __device__ __forceinline__ uint32_t candidate_mask(const uint32_t na, const uint
     return (ma & 0xFu) | ((mb & 0xFu) << 4);
 }
 
-// Exact Algorithm 2 for one interior pixel at tile position (y, x): returns
-// the replacement value, or -1 when the pixel is not replaced.  Values are
-// integers below 2^24, so the float sums are exact; rms_floor turns them
-// into the integer root mean square.
+// d = prmt(a, b, sel) in the generic mode, whose selector nibbles with bit 3
+// set replicate the sign bit of the chosen byte (not available through
+// __byte_perm).
+__device__ __forceinline__ uint32_t prmt_sign(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
+// Exact Algorithm 2 for one interior pixel at tile position (y, x), in packed
+// arithmetic: returns the replacement value, or -1 when the pixel is not
+// replaced.  cp holds c + 1/2 (c: the pixel's value) and na holds -alpha, in
+// both halves.
+//
+// Each window row is read as the B + 1 words that hold its 2B + 1 fp16
+// values.  They hold 2B + 2 halves; the one outside the window (the first
+// when the row starts at an odd column, else the last) is masked off, as are
+// the padding bytes of a last byte word that takes a single fp16 word.
+//  * Closed test: for a value v, g = |v - (c + 1/2)| - alpha is negative
+//    exactly when c - alpha < v <= c + alpha (v and c integers, |g| never
+//    0), so a byte permute that replicates the sign bits of the halves' high
+//    bytes gives 0xFF for a closed value and 0x00 for an open one.  For alpha
+//    = 0 every value is open, the pixel itself included.
+//  * Values as bytes: the fp16 number 1024 + v has v as its low byte.
+//  * With four values and their masks in one word each, the open values'
+//    squares sum in one 4-way integer dot product, and the open values are
+//    counted by a population count (8 bits per value).
 template <int B, int SW>
-__device__ __forceinline__ int exact_replacement(const __half* __restrict__ in, int y, int x, int alpha) {
-    const float ip = __half2float(in[y * SW + x]);
-    const float hi = ip + (float)alpha + 1.f;
-    const float lo = ip - (float)alpha;
-    float sum = 0.f;
-    int flag = 0;
+__device__ __forceinline__ int exact_packed(const uint32_t* __restrict__ w32, int y, int x, __half2 cp, __half2 na) {
+    constexpr int SWW = SW / 2;
+    constexpr int NW = B + 1;         // fp16 words per window row
+    constexpr int NB = (NW + 1) / 2;  // byte words per window row
+    const int h0 = x - B;             // first window column
+    const bool odd = (h0 & 1) != 0;
+    // Bytes of the row that are window values (bit pattern per byte word).
+    constexpr uint32_t kLastPad = (NW & 1) ? 0x0000FFFFu : 0xFFFFFFFFu;  // a last word of two bytes
+    const uint32_t first_ok = odd ? 0xFFFFFF00u : 0xFFFFFFFFu;
+    const uint32_t last_ok = odd ? kLastPad : (kLastPad >> 8);
+    const __half2 k1024 = __float2half2_rn(1024.f);
+    int sum = 0, open_bits = 0;
 #pragma unroll
-    for (int dy = -B; dy <= B; ++dy)
+    for (int dy = -B; dy <= B; ++dy) {
+        const uint32_t* row = w32 + (y + dy) * SWW + (h0 >> 1);
+        uint32_t w[NW];
 #pragma unroll
-        for (int dx = -B; dx <= B; ++dx) {
-            const float v = __half2float(in[(y + dy) * SW + x + dx]);
-            const bool open = !(v < hi && v > lo);
-            sum += open ? v * v : 0.f;
-            flag += open ? 1 : 0;
+        for (int i = 0; i < NW; ++i) w[i] = row[i];
+#pragma unroll
+        for (int k = 0; k < NB; ++k) {
+            const uint32_t a = w[2 * k];
+            const uint32_t b = (2 * k + 1 < NW) ? w[2 * k + 1] : 0u;
+            const uint32_t ga = h2u(__hadd2(__habs2(__hsub2(u2h(a), cp)), na));
+            const uint32_t gb = h2u(__hadd2(__habs2(__hsub2(u2h(b), cp)), na));
+            const uint32_t vb = __byte_perm(h2u(__hadd2(u2h(a), k1024)), h2u(__hadd2(u2h(b), k1024)), 0x6420u);
+            const uint32_t closed = prmt_sign(ga, gb, 0xFDB9u);
+            uint32_t ok = 0xFFFFFFFFu;
+            if (k == 0) ok &= first_ok;
+            if (k == NB - 1) ok &= last_ok;
+            const uint32_t open = ~closed & ok;
+            sum = (int)__dp4a(vb & open, vb, (unsigned)sum);
+            open_bits += __popc(open);
         }
+    }
+    const int flag = open_bits >> 3;
     constexpr int kPixCount = (2 * B + 1) * (2 * B + 1);
-    if (flag > kPixCount - 3) return rms_floor(sum, flag);
+    if (flag > kPixCount - 3) return B == 1 ? rms_floor_3x3(sum, flag) : rms_floor((float)sum, flag);
     return -1;
 }
 
@@ -313,8 +356,17 @@ struct PassCtx {
     int* nlist;          // its counter (may exceed kListCap: overflow)
     unsigned evals;      // core pixels this thread evaluated in list passes
     int x0, y0, rows, cols, alpha;
+    // Tile positions of the image pixels at least beta from every edge (the
+    // only ones that can change): ylo <= y < yhi, xlo <= x < xhi.
+    int ylo, yhi, xlo, xhi;
+    __half2 na;          // -alpha in both halves (exact_packed)
     bool changed_core;   // this lane saw a core pixel change
 };
+
+template <int B, int T>
+__device__ __forceinline__ bool interior(const PassCtx<B, T>& c, int y, int x) {
+    return y >= c.ylo && y < c.yhi && x >= c.xlo && x < c.xhi;
+}
 
 __device__ __forceinline__ bool in_core_px(int y, int x, int H, int TH, int TW) {
     return y >= H && y < H + TH && x >= kPadX && x < kPadX + TW;
@@ -335,12 +387,12 @@ __device__ __forceinline__ void flush_candidates(PassCtx<B, T>& c, const int lan
         if (i < c.ncand) {
             q = c.cand[i];
             const int y = (int)(q / G::SW), x = (int)(q - (uint32_t)y * G::SW);
-            const int gx = c.x0 + x - kPadX, gy = c.y0 + y - G::H;
-            if (gy >= B && gy < c.rows - B && gx >= B && gx < c.cols - B) {
-                const int v = exact_replacement<B, G::SW>(hin, y, x, c.alpha);
+            if (interior(c, y, x)) {
+                const __half old = hin[q];
+                const int v = exact_packed<B, G::SW>(c.in, y, x, __half2half2(__hadd(old, __float2half(0.5f))), c.na);
                 if (v >= 0) {
                     const __half hv = __int2half_rn(v);
-                    if (__half_as_ushort(hv) != __half_as_ushort(hin[q])) {
+                    if (__half_as_ushort(hv) != __half_as_ushort(old)) {
                         hout[q] = hv;
                         ch = true;
                         if (in_core_px(y, x, G::H, G::TH, G::TW)) c.changed_core = true;
@@ -596,9 +648,8 @@ __device__ __forceinline__ void list_pass(PassCtx<B, T>& c, const uint16_t* prev
         if (in_core_px(y, x, G::H, G::TH, G::TW)) ++c.evals;
         const __half old = hin[q];
         __half nv = old;
-        const int gx = c.x0 + x - kPadX, gy = c.y0 + y - G::H;
-        if (gy >= B && gy < c.rows - B && gx >= B && gx < c.cols - B) {
-            const int v = exact_replacement<B, G::SW>(hin, y, x, c.alpha);
+        if (interior(c, y, x)) {
+            const int v = exact_packed<B, G::SW>(c.in, y, x, __half2half2(__hadd(old, __float2half(0.5f))), c.na);
             if (v >= 0) nv = __int2half_rn(v);
         }
         hout[q] = nv;
@@ -691,6 +742,7 @@ fused_kernel(PassArgs a) {
     c.cand = cand;
     c.ncand = 0;
     c.alpha = a.alpha;
+    c.na = __float2half2_rn(-(float)a.alpha);
     c.evals = 0;
     unsigned* queue = &ctrl->tile_next[L & 1u];
     const int eval_max = a.tile_eval_max > 0 ? a.tile_eval_max : G::kListEvalMax;
@@ -818,6 +870,10 @@ fused_kernel(PassArgs a) {
         c.y0 = y0;
         c.rows = rows;
         c.cols = cols;
+        c.ylo = B + G::H - y0;           // gy = y0 + y - H >= B
+        c.yhi = rows - B + G::H - y0;    // gy < rows - B
+        c.xlo = B + kPadX - x0;          // gx = x0 + x - kPadX >= B
+        c.xhi = cols - B + kPadX - x0;   // gx < cols - B
         int dense_passes = 0;
         for (int t = 0; t < np; ++t) {
             c.in = (t & 1) ? buf1 : buf0;

@@ -71,14 +71,16 @@ __device__ __forceinline__ int eval_pixel(const uint8_t* p, long long stride, in
 // counts.  Each CTA arrives with one release reduction (no value returned,
 // so no round trip) and polls its counter until the low half reaches the
 // barrier's target; counters are never reset within a call, so the target
-// of the n-th use of a counter is n * nblocks.  The high half's growth since
+// of the n-th use of a counter is n * nblocks (plus `extra`, which only the
+// test of the bounded wait sets: an arrival that never comes).  The high half's growth since
 // this counter's previous use is this barrier's sum: a CTA can arrive at the
 // next barrier of the same counter only after every CTA has passed the
 // barrier in between, hence after every CTA has read this one's value.  The
 // wait is bounded; returns false (for every thread of the CTA) when it gave
 // up.
 __device__ __forceinline__ bool grid_barrier(GridBar* b, Ctrl* c, unsigned nblocks, unsigned& nbar,
-                                             const unsigned* count, unsigned (&prev_hi)[2], unsigned& total) {
+                                             const unsigned* count, unsigned (&prev_hi)[2], unsigned& total,
+                                             unsigned extra, unsigned max_spins) {
     __shared__ unsigned s_total;
     __syncthreads();
     int ok = 1;
@@ -87,7 +89,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar* b, Ctrl* c, unsigned nbloc
         const unsigned par = bn & 1u;
         unsigned long long* ctr = &b->ctr[par].v;
         const unsigned long long add = 1ull + ((unsigned long long)*count << 32);
-        const unsigned target = ((bn + 1u) >> 1) * nblocks;  // uses of this counter so far x CTAs
+        const unsigned target = ((bn + 1u) >> 1) * nblocks + extra;  // uses of this counter so far x CTAs
         __threadfence();
         asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(ctr), "l"(add) : "memory");
         unsigned spins = 0;
@@ -95,7 +97,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar* b, Ctrl* c, unsigned nbloc
         while (true) {
             asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(ctr) : "memory");
             if ((unsigned)v >= target) break;
-            if (++spins > (1u << 22)) {  // one to two seconds
+            if (++spins > max_spins) {  // built-in limit 2^22: one to two seconds
                 atomicExch(&c->error, 1u);
                 ok = 0;
                 break;
@@ -501,7 +503,8 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
         if (lane == 0 && sl.total) atomicAdd(&s_app, sl.total);
         sl.total = 0u;
         unsigned appended = 0;
-        if (!grid_barrier(a.bar, ctrl, gridDim.x, gen, &s_app, prev_hi, appended)) {
+        if (!grid_barrier(a.bar, ctrl, gridDim.x, gen, &s_app, prev_hi, appended, a.bar_extra,
+                          a.bar_spins ? a.bar_spins : (1u << 22))) {
             failed = true;
             break;
         }

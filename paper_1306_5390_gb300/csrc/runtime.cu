@@ -81,6 +81,7 @@ struct hgrms_ctx {
     int opt_tile_eval_max = 0;
     int opt_autotune = 0;
     int opt_list_ctas = 0;
+    int opt_wait_test = 0;
     std::map<long long, Tuning> tuned;  // autotuner choices by (beta, batch, size class)
     cudaEvent_t tune_ev[2] = {nullptr, nullptr};
     // Stream shared with other handles whose work overlaps this one's (the
@@ -498,6 +499,8 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
     // List-pass CTAs: one per SM below 16 M pixels (fewer CTAs at the
     // barrier; measured faster on GB300 up to 2048 x 2048), two per SM above.
     a.list_ctas = h->opt_list_ctas > 0 ? h->opt_list_ctas : (px_total < (16ll << 20) ? h->sms : 0);
+    a.bar_extra = h->opt_wait_test > 0 ? 1u : 0u;
+    a.bar_spins = (unsigned)h->opt_wait_test;
     const bool user_ppm = h->opt_relaunch_ppm > 0;
     const long long ppm = user_ppm ? h->opt_relaunch_ppm : default_relaunch_ppm(beta);
     a.relaunch_evals = ppm >= 1000000 ? (1ll << 62) : px_total / 1000000 * ppm + px_total % 1000000 * ppm / 1000000;
@@ -833,6 +836,8 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
     a.tile_eval_max = h->opt_tile_eval_max;
     a.user0 = nullptr;
     a.list_ctas = 0;
+    a.bar_extra = h->opt_wait_test > 0 ? 1u : 0u;
+    a.bar_spins = (unsigned)h->opt_wait_test;
     // Per-launch timing is limited to calls of at most kMaxTimedLaunches launches.
     constexpr int kMaxTimedLaunches = 4096;
     const bool timed = h->opt_timing && p.launches <= kMaxTimedLaunches;
@@ -1244,6 +1249,10 @@ HG_EXPORT int hgrms_set_option(hgrms_t h, int option, int value) {
         case HGRMS_OPT_AUTOTUNE:
             if (value != 0 && value != 1) return HGRMS_EINVAL;
             h->opt_autotune = value;
+            return HGRMS_OK;
+        case HGRMS_OPT_WAIT_TEST:
+            if (value < 0 || value > (1 << 22)) return HGRMS_EINVAL;
+            h->opt_wait_test = value;
             return HGRMS_OK;
         case HGRMS_OPT_TILE_EVAL_MAX:
             if (value < 0 || value > (1 << 20)) return HGRMS_EINVAL;

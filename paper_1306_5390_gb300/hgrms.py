@@ -39,6 +39,7 @@ HGRMS_OPT_AUTOTUNE = 8
 HGRMS_OPT_PREDICT_K = 9
 HGRMS_OPT_LIST_CTAS = 10
 HGRMS_OPT_GRAPH = 11
+HGRMS_OPT_WAIT_TEST = 12
 
 # Every symbol the header declares (the CPU tests check the library exports them).
 EXPORTED = (

@@ -121,3 +121,17 @@ def test_server_without_device(lib):
         lib.hgrms_server_destroy(h)
     lib.hgrms_server_destroy(None)  # accepted
     assert lib.hgrms_server_wait(None, 1, 0.0, None) == hgrms.HGRMS_EINVAL
+
+
+def test_header_constants_match_the_binding():
+    """Every #define HGRMS_* integer constant of the header has the same value
+    in the Python binding."""
+    from paper_1306_5390_gb300 import hgrms
+    text = open(HEADER).read()
+    found = 0
+    for name, val in re.findall(r"#define\s+(HGRMS_[A-Z0-9_]+)\s+\(?(-?\d+)\)?\s", text):
+        assert getattr(hgrms, name) == int(val), name
+        found += 1
+    m = re.search(r"#define\s+HGRMS_NOALLOC_SCRATCH_BYTES\s+\((\d+)u << (\d+)\)", text)
+    assert m and hgrms.HGRMS_NOALLOC_SCRATCH_BYTES == int(m.group(1)) << int(m.group(2))
+    assert found >= 20
