@@ -197,6 +197,15 @@ __device__ __forceinline__ int rms_floor_3x3(int sum, int flag) {
     return isqrt_u16((int)__umulhi((unsigned)sum, m));
 }
 
+// d = prmt(a, b, sel) in the generic mode, whose selector nibbles with bit 3
+// set replicate the sign bit of the chosen byte (not available through
+// __byte_perm).
+__device__ __forceinline__ uint32_t prmt_sign(uint32_t a, uint32_t b, uint32_t sel) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+
 // Passes the launch must run: 0 when the call has finished.
 __device__ __forceinline__ int launch_passes(const Ctrl* c, int T) {
     unsigned k = __ldcg(&c->k);

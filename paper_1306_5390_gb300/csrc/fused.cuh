@@ -244,15 +244,6 @@ __device__ __forceinline__ uint32_t candidate_mask(const uint32_t na, const uint
     return (ma & 0xFu) | ((mb & 0xFu) << 4);
 }
 
-// d = prmt(a, b, sel) in the generic mode, whose selector nibbles with bit 3
-// set replicate the sign bit of the chosen byte (not available through
-// __byte_perm).
-__device__ __forceinline__ uint32_t prmt_sign(uint32_t a, uint32_t b, uint32_t sel) {
-    uint32_t d;
-    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
-    return d;
-}
-
 // Exact Algorithm 2 for one interior pixel at tile position (y, x), in packed
 // arithmetic: returns the replacement value, or -1 when the pixel is not
 // replaced.  cp holds c + 1/2 (c: the pixel's value) and na holds -alpha, in

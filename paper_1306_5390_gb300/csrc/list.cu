@@ -34,12 +34,21 @@ namespace {
 
 constexpr int kListThreads = 512;
 
+// Loads of the bitmaps and canvases that the previous pass wrote go through
+// L1 (__ldca): nearby evaluations of one CTA read overlapping windows, and an
+// L2-only load moves a whole 32-byte sector per 4-byte word.  This is
+// coherent because every pass starts after the grid barrier, whose
+// gpu-scope acquire (thread 0) and CTA barrier order each thread's later
+// loads after every write of the previous pass - the pattern of a grid-wide
+// synchronisation, after which ordinary loads observe the other CTAs' writes.
+// Nothing a pass reads is written during the same pass.
+
 // Bits [start, start + 32) of a bitmap row (outside [0, 32 * nwords): 0).
 __device__ __forceinline__ uint32_t row_bits(const uint32_t* __restrict__ row, int nwords, int start) {
     const int w0 = start >= 0 ? (start >> 5) : -((31 - start) >> 5);
     const int sh = start - 32 * w0;
-    const uint32_t a = (w0 >= 0 && w0 < nwords) ? __ldcg(row + w0) : 0u;
-    const uint32_t b = (w0 + 1 >= 0 && w0 + 1 < nwords) ? __ldcg(row + w0 + 1) : 0u;
+    const uint32_t a = (w0 >= 0 && w0 < nwords) ? __ldca(row + w0) : 0u;
+    const uint32_t b = (w0 + 1 >= 0 && w0 + 1 < nwords) ? __ldca(row + w0 + 1) : 0u;
     return sh ? ((a >> sh) | (b << (32 - sh))) : a;
 }
 
@@ -125,7 +134,7 @@ __device__ __forceinline__ void load_row_bytes(const uint8_t* p, uint32_t (&r)[(
     const uint32_t sh = (uint32_t)(a & 3u) * 8u;
     uint32_t w[NW + 1];
 #pragma unroll
-    for (int i = 0; i <= NW; ++i) w[i] = __ldcg(q + i);
+    for (int i = 0; i <= NW; ++i) w[i] = __ldca(q + i);
 #pragma unroll
     for (int i = 0; i < NW; ++i) r[i] = __funnelshift_r(w[i], w[i + 1], sh);
 }
