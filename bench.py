@@ -402,7 +402,7 @@ def per_kernel(acc, betas, rows, cols):
         passes = {0: fused_passes, 1: a["passes_executed"] - fused_passes, 2: a["passes_executed"]}
         ev = {0: a["evals_fused"], 1: a["evals_list"], 2: a["passes_executed"] * rows * cols}
         per_beta_out[str(b)] = dict(
-            k=a["k"], converged=bool(a["converged"]), passes_per_launch=a["T"],
+            k=a["k"], converged=bool(a["converged"]), passes_per_launch=a["T"], ctas_per_launch=a["ctas"],
             work_launches_per_call=a["work_launches"] / calls,
             kernel_ms_per_call=a["kernel_ms"] / calls,
             idle_launch_ms_per_call=a["idle_kernel_ms"] / calls,

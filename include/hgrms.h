@@ -336,6 +336,10 @@ int hgrms_predictor_grad(hgrms_t h, const float* weights, const float* x0, const
                                      else as a dense pass (0 = built-in: 2048 for beta 2, else
                                      4096) */
 
+#define HGRMS_OPT_TMA      13 /* 1 = the default schedule's fused launches (beta <= 4) stage each tile
+                                   with its halo in shared memory by TMA, the next tile's load running
+                                   while the current one computes (default); 0 = ordinary loads.
+                                   Results are identical either way. */
 #define HGRMS_OPT_WAIT_TEST 12 /* for tests of the bounded device wait (not for production): N > 0 makes
                                    every grid barrier of the list-pass launch wait for one arrival more
                                    than the launch has CTAs - an arrival that never comes - and give up

@@ -4,6 +4,7 @@
 // per-launch finalisation done by the last CTA of each launch.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string.h>
@@ -158,7 +159,16 @@ struct PassArgs {
     // built-in limit of one to two seconds).
     unsigned bar_extra = 0;
     unsigned bar_spins = 0;
+    // Hybrid schedule: tensor maps for the fused kernel's tile loads by TMA,
+    // kTmaMapsPerImage per image (canvas 0, 1, 2, then the caller's image),
+    // each a 3-D view (16 bytes, 16-byte chunks of a row, rows) whose box is
+    // one tile with its halo.  Null: tiles are read with ordinary loads.
+    // tma_user: the caller's-image maps are valid (aligned device images), so
+    // the first fused launch loads from them too.
+    const CUtensorMap* tmaps = nullptr;
+    int tma_user = 0;
 };
+constexpr int kTmaMapsPerImage = 4;
 
 // floor(sqrt(floor(sum / flag))) exactly (the root mean square of Algorithm
 // 2 in integers), for 0 <= sum <= flag * 255^2 and 1 <= flag <= 225, as every

@@ -83,13 +83,21 @@ struct FusedGeo {
     static constexpr int C0 = kPadX - 8;             // first computed column
     static constexpr int CN = 256;                   // computed columns
     static constexpr int P = (2 * B + 1) * (2 * B + 1);
-    static constexpr int kCandCap = kRows / 2 * 256;  // per-warp candidate list (half a band)
+    // Band rows per candidate append (at most 256 candidates per row): beta 2
+    // appends every 4 rows (measured faster than 2), the others every 2, which
+    // keeps the lists small enough for the TMA staging buffer.
+    static constexpr int kAppendRows = B == 2 ? 4 : 2;
     // beta 3: dense passes count in two stages (band_dense2; for beta 2 the
     // single-stage count measured faster); the second half of a warp's
-    // candidate buffer then holds its stage-two work list.
+    // candidate buffer then holds its stage-two work list (at most 4 pixel
+    // pairs per lane and row of a kAppendRows-row group).
     static constexpr bool kTwoStage = B == 3 && kRows == 8;
+    static constexpr int kCandCap = kAppendRows * 256;  // per-warp candidate list
     static constexpr int kCandLimit = kTwoStage ? kCandCap / 2 : kCandCap;
-    static constexpr int kListCap = 2048;            // changed pixels kept per pass
+    // Changed pixels kept per pass: a list pass needs at most eval_max /
+    // (2 beta + 1)^2 of them at the built-in switch points (455 for beta 1,
+    // 82 for beta 2, 84 for beta 3); a longer list makes the next pass dense.
+    static constexpr int kListCap = B == 1 ? 1024 : 448;
     static constexpr int kListEvalMax = 2048;        // default: list-pass evaluations above which a pass runs dense
     static constexpr int kMarkWords = (SH * SW + 31) / 32;
     // shared memory layout (bytes)
@@ -98,11 +106,21 @@ struct FusedGeo {
     static constexpr size_t kListOff = kCandOff + (size_t)kWarps * kCandCap * sizeof(uint16_t);
     static constexpr size_t kMarkOff = kListOff + 2ull * kListCap * sizeof(uint16_t);
     static constexpr size_t kCntOff = kMarkOff + 2ull * kMarkWords * sizeof(uint32_t);
-    static constexpr size_t kSmem = kCntOff + 8 * sizeof(int);
+    static constexpr size_t kSmemBase = kCntOff + 8 * sizeof(int);
+    // TMA staging buffer: the next tile with its halo, as bytes (SH rows of SW
+    // bytes), loaded while the current tile computes.  Only when two CTAs per
+    // SM still fit (the SM's 228 KB, less 1 KB reserved per CTA and the static
+    // shared variables).
+    static constexpr size_t kStaticSmem = 192;  // the kernel's static shared variables (128 bytes) and slack
+    static constexpr size_t kStageOff = (kSmemBase + 127) / 128 * 128;
+    static constexpr size_t kStageBytes = ((size_t)SH * SW + 127) / 128 * 128;
+    static constexpr bool kTma = 2 * (kStageOff + kStageBytes + 1024 + kStaticSmem) <= 233472;
+    static constexpr size_t kSmem = kTma ? kStageOff + kStageBytes : kSmemBase;
     // Lanes 0..31 cover columns [C0, C0 + 256): results within T*beta of
     // those edges may use wrong horizontal neighbours, so T*beta <= 8 keeps
     // the core [kPadX, kPadX + TW) exact after T passes.
     static_assert(T * B <= 8, "fused halo exceeds the computed margin");
+    static_assert(SW == 17 * 16 && SH <= 256, "TMA box: 17 chunks of 16 bytes by SH rows");
     static_assert(TH >= 16, "tile too short");
     static_assert(SH * SW < 65536, "pixel index encoding");
     static_assert(C0 + 8 * 32 == kPadX + TW + 8, "strip layout");
@@ -477,10 +495,11 @@ __device__ __forceinline__ void band_dense(PassCtx<B, T>& c, const int ys, const
         const uint32_t nb = not_candidate_bits<B>(cnt.acc[2], cnt.acc[3]);
         if ((na & nb) != 0x80808080u) m64 |= (unsigned long long)candidate_mask(na, nb) << (8 * r);
     }
-    constexpr int kHalf = G::kRows / 2;  // rows per append (a half band fits the list)
-    constexpr unsigned long long kHalfMask = (1ull << (8 * kHalf)) - 1ull;
-    append_bits<B, T>(c, lane, (uint32_t)(m64 & kHalfMask), ys, 2 * ws);
-    append_bits<B, T>(c, lane, (uint32_t)((m64 >> (8 * kHalf)) & kHalfMask), ys + kHalf, 2 * ws);
+    constexpr int kA = G::kAppendRows;  // rows per append (kA * 256 candidates at most)
+    constexpr unsigned long long kAMask = (1ull << (8 * kA)) - 1ull;
+#pragma unroll
+    for (int g = 0; g < G::kRows / kA; ++g)
+        append_bits<B, T>(c, lane, (uint32_t)((m64 >> (8 * kA * g)) & kAMask), ys + kA * g, 2 * ws);
 }
 
 // Outer-ring closed-neighbour count of one pixel pair (the fp16 pair at
@@ -517,24 +536,25 @@ __device__ __forceinline__ uint32_t outer_count(const uint32_t* __restrict__ in,
     return acc;
 }
 
-// Dense pass over the warp's 8-row band in two stages (beta 3).  Stage one
-// counts every pixel's closed neighbours in the inner 3 x 3 ring, packed as
-// in band_dense; a pixel with two or more already has too many to be a
-// candidate.  The other pixels' pairs go to a per-warp work list (row,
-// lane, pair and the pixels' stage-one state: not settled, one closed
-// neighbour) and stage two counts only the outer ring for them, one pair per
-// lane.  Pixels with at most one closed neighbour in all are candidates.
+// Dense pass over the warp's 8-row band in two stages (beta 3), in groups of
+// kAppendRows rows.  Stage one counts every pixel's closed neighbours in the
+// inner 3 x 3 ring, packed as in band_dense; a pixel with two or more already
+// has too many to be a candidate.  The other pixels' pairs go to a per-warp
+// work list (row, lane, pair and the pixels' stage-one state: not settled,
+// one closed neighbour) and stage two counts only the outer ring for them,
+// one pair per lane.  Pixels with at most one closed neighbour in all are
+// candidates.
 template <int B, int T>
 __device__ __forceinline__ void band_dense2(PassCtx<B, T>& c, const int ys, const int ws, const int lane,
                                             const __half2 two_a) {
     using G = FusedGeo<B, T>;
-    constexpr int kHalf = G::kRows / 2;
+    constexpr int kHalf = G::kAppendRows;  // rows per group (its work list fits half the buffer)
     uint16_t* items = c.cand + G::kCandCap / 2;
     Row<1> win[3];
     load_row_shfl<1>(c.in + (ys - 1) * G::SWW + ws, win[1]);
     load_row_shfl<1>(c.in + ys * G::SWW + ws, win[2]);
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
+    for (int h = 0; h < G::kRows / kHalf; ++h) {
         // Stage one.  U: pixels not settled (8 bits per row), K: those of
         // them with one closed neighbour in the inner ring.
         uint32_t U = 0u, K = 0u;
@@ -652,18 +672,60 @@ __device__ __forceinline__ void list_pass(PassCtx<B, T>& c, const uint16_t* prev
     }
 }
 
+// ---- Tile loads by TMA --------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32addr(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* m) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32addr(m)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+// Thread 0: announce `bytes` of transfer on the mbarrier and start the tile
+// load (box origin: byte 0, 16-byte chunk `chunk`, row `row` of the map; a
+// box partly outside the tensor reads zeros there).
+__device__ __forceinline__ void tma_tile_load(void* dst, const CUtensorMap* map, int chunk, int row, uint64_t* m,
+                                              unsigned bytes) {
+    asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(map) : "memory");
+    // The staging buffer's previous contents were read by ordinary loads.
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32addr(m)), "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];" ::"r"(smem_u32addr(dst)),
+        "l"(map), "r"(0), "r"(chunk), "r"(row), "r"(smem_u32addr(m))
+        : "memory");
+}
+// Bounded wait for phase `parity` of the mbarrier (every thread).
+__device__ __forceinline__ bool mbar_wait(uint64_t* m, unsigned parity) {
+    for (unsigned spins = 0; spins < (1u << 22); ++spins) {
+        uint32_t ok;
+        asm volatile(
+            "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(smem_u32addr(m)), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
 // Persistent: each CTA takes tiles from a queue (one counter per launch in
 // the control block) until none are left, so a launch whose work is done, or
-// that the hybrid schedule skips, costs one short wave.
+// that the hybrid schedule skips, costs one short wave.  With tensor maps,
+// thread 0 takes the next tile from the queue as soon as the current one is
+// in shared memory and starts its TMA load into the staging buffer, so the
+// load runs while the current tile computes.
 template <int B, int T>
 __global__ void __launch_bounds__(FusedGeo<B, T>::kThreads, 2)
 fused_kernel(PassArgs a) {
     using G = FusedGeo<B, T>;
-    extern __shared__ __align__(16) uint8_t smem[];
-    __shared__ int s_np, s_tile;
+    extern __shared__ __align__(128) uint8_t smem[];
+    __shared__ int s_np, s_tile, s_staged, s_next_staged;
     __shared__ unsigned s_cur, s_aux, s_launch, s_k, s_img, s_nclr, s_nin;
     __shared__ ImgDesc s_d;
     __shared__ const uint8_t* s_user;
+    __shared__ __align__(8) uint64_t s_mbar;
     const int tid = threadIdx.x;
     const int lane = tid & 31, warp = tid >> 5;
     Ctrl* ctrl = a.ctrl;
@@ -737,36 +799,60 @@ fused_kernel(PassArgs a) {
     c.evals = 0;
     unsigned* queue = &ctrl->tile_next[L & 1u];
     const int eval_max = a.tile_eval_max > 0 ? a.tile_eval_max : G::kListEvalMax;
-    for (;;) {
-        if (tid == 0) {
-            const int t = (int)atomicAdd(queue, 1u);
-            s_tile = t;
-            if (t < a.ntiles) {
-                // The tile's image: from the image table, else the single
-                // image described by the arguments.
-                ImgDesc d;
-                unsigned img = 0;
-                if (a.imgs) {
-                    img = (unsigned)__ldg(a.tile_img + t);
-                    d = load_desc(a.imgs, img);
-                } else {
-                    d.off = 0;
-                    d.bm_off = 0;
-                    d.pitch = (int)a.pitch;
-                    d.rows = a.rows;
-                    d.cols = a.cols;
-                    d.tiles_x = a.tiles_x;
-                    d.tile0 = 0;
-                    d.bm_words = a.bm_words;
-                    d.user = nullptr;
-                }
-                s_d = d;
-                s_img = img;
-                // The first launch of the hybrid schedule reads the caller's image.
-                s_user = (a.hybrid && L == 0) ? (a.nimg > 1 ? d.user : a.user0) : nullptr;
+    uint8_t* stage = smem + G::kStageOff;
+    // Thread 0: take the next tile from the queue, publish its image and
+    // source, and start its TMA load into the staging buffer when a tensor
+    // map covers it (s_staged).
+    auto take_next = [&]() {
+        const int t = (int)atomicAdd(queue, 1u);
+        s_tile = t;
+        s_staged = 0;
+        if (t >= a.ntiles) return;
+        // The tile's image: from the image table, else the single image
+        // described by the arguments.
+        ImgDesc d;
+        unsigned img = 0;
+        if (a.imgs) {
+            img = (unsigned)__ldg(a.tile_img + t);
+            d = load_desc(a.imgs, img);
+        } else {
+            d.off = 0;
+            d.bm_off = 0;
+            d.pitch = (int)a.pitch;
+            d.rows = a.rows;
+            d.cols = a.cols;
+            d.tiles_x = a.tiles_x;
+            d.tile0 = 0;
+            d.bm_words = a.bm_words;
+            d.user = nullptr;
+        }
+        s_d = d;
+        s_img = img;
+        // The first launch of the hybrid schedule reads the caller's image.
+        const uint8_t* user = (a.hybrid && L == 0) ? (a.nimg > 1 ? d.user : a.user0) : nullptr;
+        s_user = user;
+        if constexpr (G::kTma) {
+            if (a.tmaps && (!user || a.tma_user) && (smem_u32addr(stage) & 127u) == 0) {
+                const int tile = t - d.tile0;
+                const int x0 = (tile % d.tiles_x) * G::TW, y0 = (tile / d.tiles_x) * G::TH;
+                // Box origin: canvas column x0 (image column x0 - 16) and the
+                // first halo row; in the caller's image, the same pixels.
+                const CUtensorMap* map = a.tmaps + (size_t)img * kTmaMapsPerImage + (user ? 3u : cur);
+                tma_tile_load(stage, map, user ? x0 / 16 - 1 : x0 / 16, user ? y0 - G::H : kPadY + y0 - G::H,
+                              &s_mbar, (unsigned)(G::SH * G::SW));
+                s_staged = 1;
             }
         }
-        __syncthreads();
+    };
+    if (tid == 0) {
+        if constexpr (G::kTma) {
+            if (a.tmaps) mbar_init(&s_mbar);
+        }
+        take_next();
+    }
+    __syncthreads();
+    unsigned tma_waits = 0;  // TMA loads waited for (the mbarrier's phase)
+    for (;;) {
         if (s_tile >= a.ntiles) break;
         const unsigned img = s_img;
         const long long pitch = s_d.pitch, coff = s_d.off, bm_off = s_d.bm_off;
@@ -777,14 +863,16 @@ fused_kernel(PassArgs a) {
         const int tx = tile % s_d.tiles_x;
         const int ty = tile / s_d.tiles_x;
         const int x0 = tx * G::TW, y0 = ty * G::TH;
+        const bool staged = s_staged != 0;
+        const uint8_t* user = s_user;
 
         // Tile with halo: image rows [y0 - H, y0 + TH + H), columns [x0 - 16,
         // x0 + TW + 16); always inside the canvas.  Bytes -> fp16 pairs, into
         // both buffers (a list pass leaves unevaluated pixels as they are in
         // its output buffer, so that buffer must start equal to the input).
+        bool tma_failed = false;
         {
             const uint8_t* base = src + (long long)(kPadY + y0 - G::H) * pitch + x0;
-            const uint8_t* user = s_user;
             constexpr int CH = G::SW / 16;
             auto load_chunk = [&](int i) -> uint4 {
                 const int r = i / CH, cc = i - r * CH;
@@ -805,7 +893,20 @@ fused_kernel(PassArgs a) {
                 d1[0] = lo;
                 d1[1] = hi;
             };
-            if constexpr (G::kThreads == 256) {
+            if (staged) {
+                // The TMA load started when the previous tile was set up
+                // (SH rows of SW bytes, dense).  A wait that gives up records
+                // the error, waits once more for the load to land and stops
+                // this CTA's work.
+                if (!mbar_wait(&s_mbar, tma_waits & 1u)) {
+                    tma_failed = true;
+                    if (tid == 0) atomicExch(&ctrl->error, 1u);
+                    mbar_wait(&s_mbar, tma_waits & 1u);
+                }
+                ++tma_waits;
+                for (int i = tid; i < G::SH * CH; i += G::kThreads)
+                    store_chunk(i, *reinterpret_cast<const uint4*>(stage + i * 16));
+            } else if constexpr (G::kThreads == 256) {
                 // beta >= 2 (4-5 chunks per thread): every chunk of this
                 // thread is loaded before any is converted, so that the
                 // loads are in flight together (measured faster; for beta 1,
@@ -828,7 +929,10 @@ fused_kernel(PassArgs a) {
             for (int i = tid; i < 2 * G::kMarkWords; i += G::kThreads) marks[i] = 0u;
             if (tid < 8) s_cnt[tid] = 0;
         }
-        __syncthreads();
+        if (__syncthreads_or(tma_failed)) break;
+        // The staging buffer is free again: start the next tile's load.  (Every
+        // thread has copied this tile's description into registers above.)
+        if (tid == 0) take_next();
         // Pass 0's "previous pass": the pixels the previous launch's last
         // pass changed (its map or change bitmap), listed in list 1 / counter
         // 2.  A change set that overflowed lacks some of its bits: pass 0 is
@@ -1021,6 +1125,8 @@ fused_kernel(PassArgs a) {
 // Host-side description of one compiled (beta, T) instance.
 struct FusedEntry {
     int beta, T, TH, TW;
+    int SH;    // tile rows with the halo (the TMA box height)
+    bool tma;  // the kernel stages tiles by TMA when given tensor maps
     size_t smem;
     cudaError_t (*launch)(const PassArgs&, int ctas, cudaStream_t);  // one CTA per tile
 };
@@ -1056,7 +1162,7 @@ cudaError_t launch_fused(const PassArgs& a, int ctas, cudaStream_t s) {
 template <int B, int T>
 constexpr FusedEntry fused_entry() {
     using G = FusedGeo<B, T>;
-    return FusedEntry{B, T, G::TH, G::TW, G::kSmem, &launch_fused<B, T>};
+    return FusedEntry{B, T, G::TH, G::TW, G::SH, G::kTma, G::kSmem, &launch_fused<B, T>};
 }
 
 }  // namespace hg

@@ -14,6 +14,8 @@
 //      current canvas are kept on the device, so no launch waits for the
 //      host,
 //   4. copy the current canvas back and read k with one device-to-host copy.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdlib.h>
@@ -82,6 +84,13 @@ struct hgrms_ctx {
     int opt_autotune = 0;
     int opt_list_ctas = 0;
     int opt_wait_test = 0;
+    int opt_tma = 1;
+    // Tensor maps of the fused kernel's TMA tile loads (kTmaMapsPerImage per
+    // image), on the device, and the layout they were made for.
+    CUtensorMap* tmaps = nullptr;
+    size_t tmaps_cap = 0;
+    std::vector<uint8_t> tmaps_key;
+    int tmaps_user = 0;
     std::map<long long, Tuning> tuned;  // autotuner choices by (beta, batch, size class)
     cudaEvent_t tune_ev[2] = {nullptr, nullptr};
     // Stream shared with other handles whose work overlaps this one's (the
@@ -359,6 +368,37 @@ int ensure_table(hgrms_ctx* h, size_t n, size_t tiles, bool per_image_k) {
     return HGRMS_OK;
 }
 
+// cuTensorMapEncodeTiled from the driver (looked up once; null if absent).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = []() -> PFN_cuTensorMapEncodeTiled_v12000 {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// A 3-D byte view for tile loads: (16 bytes, 16-byte chunks of a row, rows)
+// of a row-major array with `pitch` bytes per row (a multiple of 16), whose
+// box is one tile with its halo: 17 chunks (272 bytes) by `box_rows` rows.
+bool encode_tile_map(CUtensorMap* m, const void* base, long long pitch, long long rows, int box_rows) {
+    PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+    if (!enc || ((uintptr_t)base & 15u) != 0 || pitch % 16 != 0 || pitch < 16 || rows < 1) return false;
+    const cuuint64_t dims[3] = {16, (cuuint64_t)(pitch / 16), (cuuint64_t)rows};
+    const cuuint64_t strides[2] = {16, (cuuint64_t)pitch};
+    const cuuint32_t box[3] = {16, 17, (cuuint32_t)box_rows};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<void*>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Bits needed for values 0 .. v (at least 1).
 int bits_for(long long v) {
     int b = 1;
@@ -385,6 +425,78 @@ long long hybrid_bytes(const hg::FusedEntry* fe, int rows, int cols) {
     const long long crows = hg::kPadY + tiles_y * fe->TH + 16;
     const long long px = (long long)rows * cols;
     return 3 * pitch * crows + 4 * 4 * (long long)rows * ((cols + 31) / 32 + 1) + 4 * 4 * (px / 4) + 4 * tiles_x * tiles_y;
+}
+
+// Tensor maps for the fused kernel's TMA tile loads of one call (kernel `fe`,
+// images `im` laid out as h->host_desc): per image, its canvas in each of the
+// three arenas and, for an image in device memory that is 16-byte aligned
+// with a width that is a multiple of 16, the image itself (the first fused
+// launch reads it directly; the box's rows and columns outside the image read
+// zeros).  They are rebuilt only when the layout changes and uploaded in
+// stream order, outside any captured graph.  Returns false when TMA cannot be
+// used for this call (ordinary loads then); *user_ok is 1 when every image
+// the first launch reads in place has a map.
+bool ensure_tile_maps(hgrms_ctx* h, const hg::FusedEntry* fe, const BatchImg* im, int n, cudaStream_t s,
+                      int* user_ok) {
+    *user_ok = 0;
+    if (!h->opt_tma || !fe->tma || !tensor_map_encoder()) return false;
+    std::vector<uint8_t> key;
+    auto put = [&key](const void* p, size_t b) {
+        const uint8_t* c = static_cast<const uint8_t*>(p);
+        key.insert(key.end(), c, c + b);
+    };
+    put(h->canvas, sizeof(h->canvas));
+    put(&fe->SH, sizeof(fe->SH));
+    put(&fe->TH, sizeof(fe->TH));
+    put(&n, sizeof(n));
+    put(h->host_desc, (size_t)n * sizeof(hg::ImgDesc));
+    for (int i = 0; i < n; ++i) {
+        put(&im[i].ptr, sizeof(im[i].ptr));
+        put(&im[i].dev, sizeof(im[i].dev));
+    }
+    if (key == h->tmaps_key) {
+        *user_ok = h->tmaps_user;
+        return true;
+    }
+    h->tmaps_key.clear();
+    const size_t nm = (size_t)n * hg::kTmaMapsPerImage;
+    if (nm > h->tmaps_cap) {
+        if (h->tmaps) cudaFree(h->tmaps);
+        h->tmaps = nullptr;
+        h->tmaps_cap = 0;
+        if (cudaMalloc(&h->tmaps, nm * sizeof(CUtensorMap)) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        h->tmaps_cap = nm;
+    }
+    std::vector<CUtensorMap> maps(nm);
+    memset(maps.data(), 0, nm * sizeof(CUtensorMap));
+    int uok = 1;
+    for (int i = 0; i < n; ++i) {
+        const hg::ImgDesc& d = h->host_desc[i];
+        const long long tiles_y = (d.rows + fe->TH - 1) / fe->TH;
+        const long long crows = hg::kPadY + tiles_y * fe->TH + 16;
+        for (int c = 0; c < 3; ++c)
+            if (!encode_tile_map(&maps[(size_t)i * hg::kTmaMapsPerImage + c], h->canvas[c] + d.off, d.pitch, crows,
+                                 fe->SH))
+                return false;
+        if (!im[i].dev) continue;  // copied into canvas 0 first
+        cudaPointerAttributes at;
+        bool ok = cudaPointerGetAttributes(&at, im[i].ptr) == cudaSuccess && at.type == cudaMemoryTypeDevice;
+        if (!ok) cudaGetLastError();
+        ok = ok && d.cols % 16 == 0 &&
+             encode_tile_map(&maps[(size_t)i * hg::kTmaMapsPerImage + 3], im[i].ptr, d.cols, d.rows, fe->SH);
+        if (!ok) uok = 0;
+    }
+    if (cudaMemcpyAsync(h->tmaps, maps.data(), nm * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    h->tmaps_key = std::move(key);
+    h->tmaps_user = uok;
+    *user_ok = uok;
+    return true;
 }
 
 // The hybrid schedule (one fused launch of T passes over the tiles of every
@@ -496,6 +608,13 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
     a.hybrid = 1;
     a.tile_eval_max = tu.eval_max;
     a.user0 = (n == 1 && im[0].dev) ? im[0].ptr : nullptr;
+    {
+        int user_ok = 0;
+        if (ensure_tile_maps(h, fe, im, n, s, &user_ok)) {
+            a.tmaps = h->tmaps;
+            a.tma_user = user_ok;
+        }
+    }
     // List-pass CTAs: one per SM below 16 M pixels (fewer CTAs at the
     // barrier; measured faster on GB300 up to 2048 x 2048), two per SM above.
     a.list_ctas = h->opt_list_ctas > 0 ? h->opt_list_ctas : (px_total < (16ll << 20) ? h->sms : 0);
@@ -976,6 +1095,7 @@ HG_EXPORT void hgrms_destroy(hgrms_t h) {
             if (h->canvas[i]) cudaFree(h->canvas[i]);
         if (h->ctrl) cudaFree(h->ctrl);
         if (h->bar) cudaFree(h->bar);
+        if (h->tmaps) cudaFree(h->tmaps);
         if (h->chg_maps) cudaFree(h->chg_maps);
         if (h->lists) cudaFree(h->lists);
         if (h->bitmaps) cudaFree(h->bitmaps);
@@ -1249,6 +1369,10 @@ HG_EXPORT int hgrms_set_option(hgrms_t h, int option, int value) {
         case HGRMS_OPT_AUTOTUNE:
             if (value != 0 && value != 1) return HGRMS_EINVAL;
             h->opt_autotune = value;
+            return HGRMS_OK;
+        case HGRMS_OPT_TMA:
+            if (value != 0 && value != 1) return HGRMS_EINVAL;
+            h->opt_tma = value;
             return HGRMS_OK;
         case HGRMS_OPT_WAIT_TEST:
             if (value < 0 || value > (1 << 22)) return HGRMS_EINVAL;

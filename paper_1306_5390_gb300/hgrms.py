@@ -40,6 +40,7 @@ HGRMS_OPT_PREDICT_K = 9
 HGRMS_OPT_LIST_CTAS = 10
 HGRMS_OPT_GRAPH = 11
 HGRMS_OPT_WAIT_TEST = 12
+HGRMS_OPT_TMA = 13
 
 # Every symbol the header declares (the CPU tests check the library exports them).
 EXPORTED = (

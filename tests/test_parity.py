@@ -354,3 +354,26 @@ def test_golden_worked_examples_on_gpu(den, torch_cuda, name):
         out, k, conv = gpu_denoise(den, torch_cuda, g["input"], g["alpha"], g["beta"], g["max_k"], kernel=kernel)
         assert k == g["k"] and conv == bool(g["converged"]), (name, kernel, k, conv)
         np.testing.assert_array_equal(out, g["output"], err_msg=f"{name} kernel {kernel}")
+
+
+@pytest.mark.parametrize("beta", [1, 2, 3, 4, 5])
+def test_tma_staging_on_and_off_identical(oracle_mod, den, torch_cuda, beta):
+    """Tiles staged by TMA (HGRMS_OPT_TMA 1, the default) and by ordinary
+    loads (0) give the oracle's bytes and k: device images whose width is a
+    multiple of 16 (the first launch loads them by TMA too), widths that are
+    not (the first launch falls back to ordinary loads), host images (copied
+    into the canvas, then TMA), and beta 5 (no staging buffer fits)."""
+    from paper_1306_5390_gb300 import hgrms
+    torch = torch_cuda
+    shapes = [(300, 512), (257, 333), (64, 16)]
+    try:
+        for i, (r, c) in enumerate(shapes):
+            _, noisy = synth.noisy_image(r, c, 0.3, synth.seed_for(61, 10 * beta + i))
+            ref, k_ref, c_ref = oracle_mod.denoise(noisy, 10, beta, 12)
+            for tma in (1, 0):
+                den.set_option(hgrms.HGRMS_OPT_TMA, tma)
+                for host in (False, True):
+                    out, k, conv = gpu_denoise(den, torch, noisy, 10, beta, 12, host=host)
+                    assert k == k_ref and conv == c_ref and np.array_equal(out, ref), (r, c, tma, host)
+    finally:
+        den.set_option(hgrms.HGRMS_OPT_TMA, 1)
