@@ -23,6 +23,7 @@
 #include <algorithm>
 #include <cmath>
 #include <map>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -99,6 +100,8 @@ struct hgrms_ctx {
     // share the device.  Null: the handle's own stream.
     cudaStream_t coop_stream = nullptr;
     cudaEvent_t coop_ev[2] = {nullptr, nullptr};
+    // Recorded after this handle's latest list-pass launch (see chain_coop).
+    cudaEvent_t chain_ev = nullptr;
     // Learned k-predictor (weights loaded by hgrms_predictor_load) and its
     // image table.
     hg::Predictor* pred[hg::kMaxBeta + 1] = {};  // by beta
@@ -166,6 +169,39 @@ long long default_relaunch_ppm(int beta) {
 
 using hg::default_passes;
 using hg::find_fused;
+
+// Cooperative list-pass launches of every handle of the process on one device
+// run one after another, in the order they are issued.  The CTAs of such a
+// launch wait for one another at every pass, so two of them overlapping on
+// the device could each hold SM slots that the other's CTAs need, and both
+// would wait until their bounded barrier gives up.  Each launch (or replayed
+// graph that holds one) first makes its stream wait for the event recorded
+// after the previous one, whichever stream and handle that was.
+constexpr int kMaxChainDevices = 64;
+std::mutex g_chain_mu;
+cudaEvent_t g_chain_last[kMaxChainDevices] = {};
+cudaStream_t g_chain_stream[kMaxChainDevices] = {};
+
+// Run `launch` (which queues work holding a cooperative launch on stream s)
+// behind the device's previous cooperative launch, then record h->chain_ev
+// after it.  Not for use while a stream is being captured.
+template <class F>
+cudaError_t chain_coop(hgrms_ctx* h, cudaStream_t s, F&& launch) {
+    const int dev = h->device;
+    if (dev < 0 || dev >= kMaxChainDevices) return launch();
+    std::lock_guard<std::mutex> lock(g_chain_mu);
+    cudaError_t e = cudaSuccess;
+    if (!h->chain_ev) e = cudaEventCreateWithFlags(&h->chain_ev, cudaEventDisableTiming);
+    if (e == cudaSuccess && g_chain_last[dev] && g_chain_stream[dev] != s)
+        e = cudaStreamWaitEvent(s, g_chain_last[dev], 0);
+    if (e == cudaSuccess) e = launch();
+    if (e == cudaSuccess) e = cudaEventRecord(h->chain_ev, s);
+    if (e == cudaSuccess) {
+        g_chain_last[dev] = h->chain_ev;
+        g_chain_stream[dev] = s;
+    }
+    return e;
+}
 
 int cuda_fail(hgrms_ctx* h, cudaError_t e) {
     h->last_cuda_error = (int)e;
@@ -678,12 +714,17 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
                 NvtxRange nr("hgrms list-pass launch");
                 HG_TRY(h, cudaEventRecord(h->coop_ev[0], s));
                 HG_TRY(h, cudaStreamWaitEvent(h->coop_stream, h->coop_ev[0], 0));
-                HG_TRY(h, hg::launch_list(beta, a, h->sms, h->coop_stream));
+                HG_TRY(h, chain_coop(h, h->coop_stream,
+                                     [&] { return hg::launch_list(beta, a, h->sms, h->coop_stream); }));
                 HG_TRY(h, cudaEventRecord(h->coop_ev[1], h->coop_stream));
                 HG_TRY(h, cudaStreamWaitEvent(s, h->coop_ev[1], 0));
-            } else {
+            } else if (capturing) {
+                // The replay of the recorded graph is chained as a whole.
                 NvtxRange nr("hgrms list-pass launch");
                 HG_TRY(h, hg::launch_list(beta, a, h->sms, s));
+            } else {
+                NvtxRange nr("hgrms list-pass launch");
+                HG_TRY(h, chain_coop(h, s, [&] { return hg::launch_list(beta, a, h->sms, s); }));
             }
             if (timed) HG_TRY(h, record(h->events[2 * i + 1]));
         }
@@ -737,7 +778,10 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
             if (g) cudaGraphDestroy(g);
         }
         if (ex) {
-            HG_TRY(h, cudaGraphLaunch(ex, s));
+            if (list_loop)
+                HG_TRY(h, chain_coop(h, s, [&] { return cudaGraphLaunch(ex, s); }));
+            else
+                HG_TRY(h, cudaGraphLaunch(ex, s));
         } else {
             rc = enqueue(s, false);
             if (rc < 0) return rc;
@@ -969,7 +1013,7 @@ int denoise_one(hgrms_ctx* h, uint8_t* img, int rows, int cols, int alpha, int b
         if (i < p.fused_launches)
             HG_TRY(h, p.fe->launch(a, p.tiles_x * p.tiles_y, s));
         else if (p.fused)
-            HG_TRY(h, hg::launch_list(beta, a, h->sms, s));
+            HG_TRY(h, chain_coop(h, s, [&] { return hg::launch_list(beta, a, h->sms, s); }));
         else
             HG_TRY(h, hg::launch_plain(beta, a, s));
         if (timed) HG_TRY(h, cudaEventRecord(h->events[2 * i + 1], s));
@@ -1110,6 +1154,12 @@ HG_EXPORT void hgrms_destroy(hgrms_t h) {
             if (e) cudaEventDestroy(e);
         for (cudaEvent_t e : h->coop_ev)
             if (e) cudaEventDestroy(e);
+        if (h->chain_ev) {
+            std::lock_guard<std::mutex> lock(g_chain_mu);
+            if (h->device >= 0 && h->device < kMaxChainDevices && g_chain_last[h->device] == h->chain_ev)
+                g_chain_last[h->device] = nullptr;
+            cudaEventDestroy(h->chain_ev);
+        }
         for (auto& g : h->graphs) cudaGraphExecDestroy(g.second);
         if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
         for (hg::Predictor* p : h->pred) hg::predictor_free(p);
