@@ -5,7 +5,9 @@
 // future work.  The estimate only chooses a schedule; results and k are
 // always those of the exact method.
 //
-// Network (weights from an offline fit on oracle-labelled images):
+// Network (weights from an offline fit on seeded synthetic images labelled
+// with k by this library's exact denoiser; a sample of the labels is checked
+// against the CPU oracle by the tests):
 //   x0 = 64 x 64 x 1 area means / 255
 //   x1..x4 = ReLU(conv3x3(x_{l-1}) + b_l), 16 channels, zero padding
 //   g = mean of x4 over the 64 x 64 positions (16 values)
