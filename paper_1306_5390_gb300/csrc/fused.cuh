@@ -262,9 +262,9 @@ __device__ __forceinline__ uint32_t candidate_mask(const uint32_t na, const uint
     return (ma & 0xFu) | ((mb & 0xFu) << 4);
 }
 
-// Exact Algorithm 2 for one interior pixel at tile position (y, x), in packed
-// arithmetic: returns the replacement value, or -1 when the pixel is not
-// replaced.  cp holds c + 1/2 (c: the pixel's value) and na holds -alpha, in
+// Exact Algorithm 2 for one interior pixel at tile index q = y * SW + x, in
+// packed arithmetic: returns the replacement value, or -1 when the pixel is
+// not replaced.  cp holds c + 1/2 (c: the pixel's value) and na holds -alpha, in
 // both halves.
 //
 // Each window row is read as the B + 1 words that hold its 2B + 1 fp16
@@ -281,11 +281,13 @@ __device__ __forceinline__ uint32_t candidate_mask(const uint32_t na, const uint
 //    squares sum in one 4-way integer dot product, and the open values are
 //    counted by a population count (8 bits per value).
 template <int B, int SW>
-__device__ __forceinline__ int exact_packed(const uint32_t* __restrict__ w32, int y, int x, __half2 cp, __half2 na) {
+__device__ __forceinline__ int exact_packed(const uint32_t* __restrict__ w32, int q, __half2 cp, __half2 na) {
     constexpr int SWW = SW / 2;
     constexpr int NW = B + 1;         // fp16 words per window row
     constexpr int NB = (NW + 1) / 2;  // byte words per window row
-    const int h0 = x - B;             // first window column
+    // q = y * SW + x; the window's first value of row y + dy is half q - B +
+    // dy * SW, i.e. (SW even) word ((q - B) >> 1) + dy * SWW, at the parity of q - B.
+    const int h0 = q - B;
     const bool odd = (h0 & 1) != 0;
     // Bytes of the row that are window values (bit pattern per byte word).
     constexpr uint32_t kLastPad = (NW & 1) ? 0x0000FFFFu : 0xFFFFFFFFu;  // a last word of two bytes
@@ -295,7 +297,7 @@ __device__ __forceinline__ int exact_packed(const uint32_t* __restrict__ w32, in
     int sum = 0, open_bits = 0;
 #pragma unroll
     for (int dy = -B; dy <= B; ++dy) {
-        const uint32_t* row = w32 + (y + dy) * SWW + (h0 >> 1);
+        const uint32_t* row = w32 + (h0 >> 1) + dy * SWW;
         uint32_t w[NW];
 #pragma unroll
         for (int i = 0; i < NW; ++i) w[i] = row[i];
@@ -368,6 +370,7 @@ struct PassCtx {
     // Tile positions of the image pixels at least beta from every edge (the
     // only ones that can change): ylo <= y < yhi, xlo <= x < xhi.
     int ylo, yhi, xlo, xhi;
+    bool all_interior;   // every computed position of the tile is interior
     __half2 na;          // -alpha in both halves (exact_packed)
     bool changed_core;   // this lane saw a core pixel change
 };
@@ -395,16 +398,24 @@ __device__ __forceinline__ void flush_candidates(PassCtx<B, T>& c, const int lan
         uint32_t q = 0;
         if (i < c.ncand) {
             q = c.cand[i];
-            const int y = (int)(q / G::SW), x = (int)(q - (uint32_t)y * G::SW);
-            if (interior(c, y, x)) {
+            bool inner = c.all_interior;
+            if (!inner) {
+                const int y = (int)(q / G::SW), x = (int)(q - (uint32_t)y * G::SW);
+                inner = interior(c, y, x);
+            }
+            if (inner) {
                 const __half old = hin[q];
-                const int v = exact_packed<B, G::SW>(c.in, y, x, __half2half2(__hadd(old, __float2half(0.5f))), c.na);
+                const int v = exact_packed<B, G::SW>(c.in, (int)q, __half2half2(__hadd(old, __float2half(0.5f))), c.na);
                 if (v >= 0) {
                     const __half hv = __int2half_rn(v);
                     if (__half_as_ushort(hv) != __half_as_ushort(old)) {
                         hout[q] = hv;
                         ch = true;
-                        if (in_core_px(y, x, G::H, G::TH, G::TW)) c.changed_core = true;
+                        // Whether a core pixel changed: decoded until this lane has seen one.
+                        if (!c.changed_core) {
+                            const int y = (int)(q / G::SW), x = (int)(q - (uint32_t)y * G::SW);
+                            c.changed_core = in_core_px(y, x, G::H, G::TH, G::TW);
+                        }
                     }
                 }
             }
@@ -660,7 +671,7 @@ __device__ __forceinline__ void list_pass(PassCtx<B, T>& c, const uint16_t* prev
         const __half old = hin[q];
         __half nv = old;
         if (interior(c, y, x)) {
-            const int v = exact_packed<B, G::SW>(c.in, y, x, __half2half2(__hadd(old, __float2half(0.5f))), c.na);
+            const int v = exact_packed<B, G::SW>(c.in, q, __half2half2(__hadd(old, __float2half(0.5f))), c.na);
             if (v >= 0) nv = __int2half_rn(v);
         }
         hout[q] = nv;
@@ -969,6 +980,7 @@ fused_kernel(PassArgs a) {
         c.yhi = rows - B + G::H - y0;    // gy < rows - B
         c.xlo = B + kPadX - x0;          // gx = x0 + x - kPadX >= B
         c.xhi = cols - B + kPadX - x0;   // gx < cols - B
+        c.all_interior = c.ylo <= G::R0 && c.yhi >= G::R0 + G::RN && c.xlo <= G::C0 && c.xhi >= G::C0 + G::CN;
         int dense_passes = 0;
         for (int t = 0; t < np; ++t) {
             c.in = (t & 1) ? buf1 : buf0;
