@@ -732,7 +732,7 @@ __global__ void __launch_bounds__(FusedGeo<B, T>::kThreads, 2)
 fused_kernel(PassArgs a) {
     using G = FusedGeo<B, T>;
     extern __shared__ __align__(128) uint8_t smem[];
-    __shared__ int s_np, s_tile, s_staged, s_next_staged;
+    __shared__ int s_np, s_tile, s_staged;
     __shared__ unsigned s_cur, s_aux, s_launch, s_k, s_img, s_nclr, s_nin;
     __shared__ ImgDesc s_d;
     __shared__ const uint8_t* s_user;
