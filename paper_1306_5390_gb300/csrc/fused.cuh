@@ -513,6 +513,156 @@ __device__ __forceinline__ void band_dense(PassCtx<B, T>& c, const int ys, const
         append_bits<B, T>(c, lane, (uint32_t)((m64 >> (8 * kA * g)) & kAMask), ys + kA * g, 2 * ws);
 }
 
+// ---- Symmetric count (beta 1 and 2) --------------------------------------
+// The dense passes only need to know which pixels have at most one closed
+// neighbour.  Algorithm 1's own test, |I_n - I_p| < alpha, implies the closed
+// test of Algorithm 2 (I_p - alpha < I_n <= I_p + alpha), so a pixel with at
+// most one closed neighbour has at most one neighbour passing it: counting
+// with it keeps every candidate (the few extra ones, whose neighbours differ
+// by exactly alpha, the exact evaluation turns away).  And it is symmetric,
+// so each unordered pair of pixels is tested once and the result counts for
+// both.  Row y tests its "forward" pairs - (0, dx) for dx = 1..B and (dy, dx)
+// for dy = 1..B, dx = -B..B - and adds each result to row y's counts and,
+// moved by dx pixels, to row y + dy's.  One fp16x2 test covers a pixel pair:
+// sat(2 alpha - 1 - 2 |v_n - v_p|) is 1 for |v_n - v_p| <= alpha - 1 and +0
+// otherwise (exact integers in fp16; for alpha = 0 it is always 0).
+
+// Results R[j] (first endpoints: pixels 2j, 2j + 1 of the lane's segment)
+// moved by DX pixels: word j of the result covers second endpoints 2j + DX,
+// 2j + 1 + DX.  Words that cross into the neighbouring lane's segment come by
+// shuffle (lanes 0 and 31 get wrong values there, which only reach pixels
+// within B of the computed region's edge, outside the exact region).
+template <int DX>
+__device__ __forceinline__ void shifted_words(const uint32_t (&r)[4], uint32_t (&s)[4]) {
+    static_assert(DX >= -2 && DX <= 2, "beta <= 2");
+    if constexpr (DX == 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) s[j] = r[j];
+    } else if constexpr (DX == 2) {
+        const uint32_t nb = __shfl_up_sync(0xffffffffu, r[3], 1);
+        s[0] = nb; s[1] = r[0]; s[2] = r[1]; s[3] = r[2];
+    } else if constexpr (DX == -2) {
+        const uint32_t nb = __shfl_down_sync(0xffffffffu, r[0], 1);
+        s[0] = r[1]; s[1] = r[2]; s[2] = r[3]; s[3] = nb;
+    } else if constexpr (DX == 1) {
+        const uint32_t nb = __shfl_up_sync(0xffffffffu, r[3], 1);
+        s[0] = __byte_perm(nb, r[0], 0x5432);
+        s[1] = __byte_perm(r[0], r[1], 0x5432);
+        s[2] = __byte_perm(r[1], r[2], 0x5432);
+        s[3] = __byte_perm(r[2], r[3], 0x5432);
+    } else {  // DX == -1
+        const uint32_t nb = __shfl_down_sync(0xffffffffu, r[0], 1);
+        s[0] = __byte_perm(r[0], r[1], 0x5432);
+        s[1] = __byte_perm(r[1], r[2], 0x5432);
+        s[2] = __byte_perm(r[2], r[3], 0x5432);
+        s[3] = __byte_perm(r[3], nb, 0x5432);
+    }
+}
+
+// One forward direction (DY, DX) of row y: test it, add the results to the
+// counts of row y (when y is in the band: TO_Y) and of row y + DY (TO_YD).
+template <int B, int DY, int DX, bool TO_Y, bool TO_YD>
+__device__ __forceinline__ void sym_dir(const Row<B>& ry, const Row<B>& ryd, const __half2 lim,
+                                        uint32_t (&ky)[4], uint32_t (&kyd)[4]) {
+    if constexpr (TO_Y || TO_YD) {
+        const __half2 m2 = __float2half2_rn(-2.f);
+        uint32_t r[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const __half2 e = __hsub2(u2h(ryd.p[2 * j + DX + B]), u2h(ry.p[2 * j + B]));
+            r[j] = h2u(__hfma2_sat(__habs2(e), m2, lim));
+        }
+        if constexpr (TO_Y) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) ky[j] += r[j];
+        }
+        if constexpr (TO_YD) {
+            uint32_t sh[4];
+            shifted_words<DX>(r, sh);
+#pragma unroll
+            for (int j = 0; j < 4; ++j) kyd[j] += sh[j];
+        }
+    }
+}
+
+// All forward directions of band row R (R < 0: a row above the band, whose
+// own counts are not needed).
+template <int B, int T, int R>
+__device__ __forceinline__ void sym_row(const Row<B> (&win)[B + 1], const __half2 lim, uint32_t (&k)[B + 1][4]) {
+    constexpr int kRows = FusedGeo<B, T>::kRows;
+    constexpr bool kIn = R >= 0;
+    // same row: both endpoints in row y
+    sym_dir<B, 0, 1, kIn, kIn>(win[0], win[0], lim, k[0], k[0]);
+    if constexpr (B == 2) sym_dir<B, 0, 2, kIn, kIn>(win[0], win[0], lim, k[0], k[0]);
+    // rows below: second endpoint in row y + dy (only when that row is in the band)
+    constexpr bool d1 = R + 1 >= 0 && R + 1 < kRows;
+    sym_dir<B, 1, -1, kIn, d1>(win[0], win[1], lim, k[0], k[1]);
+    sym_dir<B, 1, 0, kIn, d1>(win[0], win[1], lim, k[0], k[1]);
+    sym_dir<B, 1, 1, kIn, d1>(win[0], win[1], lim, k[0], k[1]);
+    if constexpr (B == 2) {
+        sym_dir<B, 1, -2, kIn, d1>(win[0], win[1], lim, k[0], k[1]);
+        sym_dir<B, 1, 2, kIn, d1>(win[0], win[1], lim, k[0], k[1]);
+        constexpr bool d2 = R + 2 >= 0 && R + 2 < kRows;
+        sym_dir<B, 2, -2, kIn, d2>(win[0], win[2], lim, k[0], k[B]);
+        sym_dir<B, 2, -1, kIn, d2>(win[0], win[2], lim, k[0], k[B]);
+        sym_dir<B, 2, 0, kIn, d2>(win[0], win[2], lim, k[0], k[B]);
+        sym_dir<B, 2, 1, kIn, d2>(win[0], win[2], lim, k[0], k[B]);
+        sym_dir<B, 2, 2, kIn, d2>(win[0], win[2], lim, k[0], k[B]);
+    }
+}
+
+template <int B, int T, int R>
+__device__ __forceinline__ void sym_band_row(PassCtx<B, T>& c, const int ys, const int ws, const __half2 lim,
+                                             Row<B> (&win)[B + 1], uint32_t (&k)[B + 1][4],
+                                             unsigned long long& m64) {
+    using G = FusedGeo<B, T>;
+    if constexpr (R < G::kRows) {
+        // win[i] holds row ys + R + i.
+        sym_row<B, T, R>(win, lim, k);
+        if constexpr (R >= 0) {
+            const uint4 centre = make_uint4(win[0].p[B], win[0].p[B + 2], win[0].p[B + 4], win[0].p[B + 6]);
+            *reinterpret_cast<uint4*>(c.out + (ys + R) * G::SWW + ws) = centre;
+            const uint32_t na = not_candidate_bits<B>(k[0][0], k[0][1]);
+            const uint32_t nb = not_candidate_bits<B>(k[0][2], k[0][3]);
+            if ((na & nb) != 0x80808080u) m64 |= (unsigned long long)candidate_mask(na, nb) << (8 * R);
+        }
+        // Next row: counts and window move up one row.
+#pragma unroll
+        for (int i = 0; i < B; ++i) {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) k[i][j] = k[i + 1][j];
+            win[i] = win[i + 1];
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) k[B][j] = 0u;
+        if constexpr (R + 1 < G::kRows) load_row_shfl<B>(c.in + (ys + R + 1 + B) * G::SWW + ws, win[B]);
+        sym_band_row<B, T, R + 1>(c, ys, ws, lim, win, k, m64);
+    }
+}
+
+// Dense pass over the warp's band with the symmetric count (beta 1, 2).
+template <int B, int T>
+__device__ __forceinline__ void band_dense_sym(PassCtx<B, T>& c, const int ys, const int ws, const int lane) {
+    using G = FusedGeo<B, T>;
+    static_assert(B == 1 || B == 2, "symmetric count for beta 1 and 2");
+    const __half2 lim = __float2half2_rn(2.f * (float)c.alpha - 1.f);
+    Row<B> win[B + 1];
+    uint32_t k[B + 1][4];
+#pragma unroll
+    for (int i = 0; i <= B; ++i) {
+        load_row_shfl<B>(c.in + (ys - B + i) * G::SWW + ws, win[i]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) k[i][j] = 0u;
+    }
+    unsigned long long m64 = 0ull;
+    sym_band_row<B, T, -B>(c, ys, ws, lim, win, k, m64);
+    constexpr int kA = G::kAppendRows;
+    constexpr unsigned long long kAMask = (1ull << (8 * kA)) - 1ull;
+#pragma unroll
+    for (int g = 0; g < G::kRows / kA; ++g)
+        append_bits<B, T>(c, lane, (uint32_t)((m64 >> (8 * kA * g)) & kAMask), ys + kA * g, 2 * ws);
+}
+
 // Outer-ring closed-neighbour count of one pixel pair (the fp16 pair at
 // word xw of tile row y): the window positions with |dy| >= 2 or |dx| >= 2,
 // summed as integers (see the header; 40 results for beta 3).
@@ -1000,6 +1150,8 @@ fused_kernel(PassArgs a) {
                 ++dense_passes;
                 if constexpr (G::kTwoStage)
                     band_dense2<B, T>(c, ys, ws, lane, two_a);
+                else if constexpr (B <= 2)
+                    band_dense_sym<B, T>(c, ys, ws, lane);
                 else
                     band_dense<B, T>(c, ys, ws, lane, two_a);
                 flush_candidates<B, T>(c, lane);
