@@ -77,3 +77,28 @@ def test_two_stage_decision_table():
                 b_hi = (acc2 * 47 % 2**32) >> 24
                 cand_hi = unsettled and b_hi < (4 if k_in == 1 else 8)
                 assert cand_hi == (k_in + k_out <= 1), (k_in, k_out, k_other, "hi")
+
+
+def test_symmetric_pair_test_fp16_exhaustive():
+    """The symmetric count (beta 1 and 2) tests each unordered pixel pair once
+    with sat(2 alpha - 1 - 2 |v_n - v_p|) in fp16x2: an fp16 subtraction of
+    the two values, then one fused multiply-add with saturation.  For every
+    pair of 8-bit values and every alpha it must be exactly 1.0 when
+    |v_n - v_p| < alpha (Algorithm 1's test) and +0 otherwise, with the
+    roundings of fp16 arithmetic; and that test must imply Algorithm 2's
+    closed test (v_p - alpha < v_n <= v_p + alpha), so that a pixel with at
+    most one closed neighbour has at most one neighbour passing it."""
+    import numpy as np
+    v = np.arange(256, dtype=np.float16)
+    vp, vn = np.meshgrid(v, v, indexing="ij")
+    e = (vn - vp).astype(np.float16)              # exact: integers within +-255
+    assert np.array_equal(e.astype(np.int32), vn.astype(np.int32) - vp.astype(np.int32))
+    ip, inn = vp.astype(np.int32), vn.astype(np.int32)
+    for alpha in range(256):
+        lim = np.float16(2 * alpha - 1)
+        # fma rounds once: |e| * -2 + lim is an integer of magnitude below 2048, exact in fp16
+        f = np.clip((np.abs(e).astype(np.float64) * -2.0 + float(lim)).astype(np.float16), 0, 1)
+        strict = np.abs(inn - ip) < alpha
+        assert np.array_equal(f == 1, strict) and np.all((f == 0) | (f == 1)), alpha
+        closed = (inn > ip - alpha) & (inn <= ip + alpha)
+        assert not np.any(strict & ~closed), alpha
