@@ -89,6 +89,8 @@ struct hgrms_ctx {
     // Tensor maps of the fused kernel's TMA tile loads (kTmaMapsPerImage per
     // image), on the device, and the layout they were made for.
     CUtensorMap* tmaps = nullptr;
+    CUtensorMap* tmaps_host = nullptr;  // page-locked staging of the maps' upload
+    cudaEvent_t tmaps_ev = nullptr;     // recorded after the upload from tmaps_host
     size_t tmaps_cap = 0;
     std::vector<uint8_t> tmaps_key;
     int tmaps_user = 0;
@@ -317,18 +319,41 @@ int make_plan(hgrms_ctx* h, int rows, int cols, int beta, int max_k, Plan* p) {
     return HGRMS_OK;
 }
 
+// The handle's buffers grow geometrically (to at least 1.5 times their old
+// size), so that a stream of calls of slowly growing size - the request
+// server's batches - reallocates rarely: cudaFree waits for the whole device.
+// A growth that does not fit falls back to the exact size.
+size_t grown(size_t need, size_t have) {
+    return have > 0 && need < have + have / 2 ? have + have / 2 : need;
+}
+// cudaMalloc of `want` bytes (a grown size), else of `need` bytes; *got
+// receives the size allocated.
+cudaError_t malloc_grown(void** p, size_t want, size_t need, size_t* got) {
+    cudaError_t e = cudaMalloc(p, want);
+    if (e == cudaErrorMemoryAllocation && want > need) {
+        cudaGetLastError();
+        want = need;
+        e = cudaMalloc(p, want);
+    }
+    *got = e == cudaSuccess ? want : 0;
+    return e;
+}
+
 int ensure_canvas(hgrms_ctx* h, size_t bytes) {
     if (bytes <= h->canvas_bytes) return HGRMS_OK;
+    size_t got = grown(bytes, h->canvas_bytes);
     for (int i = 0; i < 3; ++i) {
         if (h->canvas[i]) cudaFree(h->canvas[i]);
         h->canvas[i] = nullptr;
     }
     h->canvas_bytes = 0;
     for (int i = 0; i < 3; ++i) {
-        HG_TRY(h, cudaMalloc(&h->canvas[i], bytes));
-        HG_TRY(h, cudaMemsetAsync(h->canvas[i], 0, bytes, h->stream));
+        size_t g = 0;
+        HG_TRY(h, malloc_grown(reinterpret_cast<void**>(&h->canvas[i]), got, bytes, &g));
+        got = g;  // a later canvas never asks for more than an earlier one got
     }
-    h->canvas_bytes = bytes;
+    for (int i = 0; i < 3; ++i) HG_TRY(h, cudaMemsetAsync(h->canvas[i], 0, got, h->stream));
+    h->canvas_bytes = got;
     return HGRMS_OK;
 }
 
@@ -344,18 +369,24 @@ int ensure_maps(hgrms_ctx* h, size_t bytes) {
 
 int ensure_lists(hgrms_ctx* h, size_t cap, size_t bm_words) {
     if (cap > h->list_cap) {
+        const size_t want = grown(cap, h->list_cap);
         if (h->lists) cudaFree(h->lists);
         h->lists = nullptr;
         h->list_cap = 0;
-        HG_TRY(h, cudaMalloc(&h->lists, 4 * cap * sizeof(uint32_t)));
-        h->list_cap = cap;
+        size_t got = 0;
+        HG_TRY(h, malloc_grown(reinterpret_cast<void**>(&h->lists), 4 * want * sizeof(uint32_t),
+                               4 * cap * sizeof(uint32_t), &got));
+        h->list_cap = got / (4 * sizeof(uint32_t));
     }
     if (bm_words > h->bitmap_words) {
+        const size_t want = grown(bm_words, h->bitmap_words);
         if (h->bitmaps) cudaFree(h->bitmaps);
         h->bitmaps = nullptr;
         h->bitmap_words = 0;
-        HG_TRY(h, cudaMalloc(&h->bitmaps, 4 * bm_words * sizeof(uint32_t)));
-        h->bitmap_words = bm_words;
+        size_t got = 0;
+        HG_TRY(h, malloc_grown(reinterpret_cast<void**>(&h->bitmaps), 4 * want * sizeof(uint32_t),
+                               4 * bm_words * sizeof(uint32_t), &got));
+        h->bitmap_words = got / (4 * sizeof(uint32_t));
     }
     return HGRMS_OK;
 }
@@ -373,6 +404,7 @@ int ensure_events(hgrms_ctx* h, size_t n) {
 // `tiles` fused tiles; a reallocation invalidates the cached table.
 int ensure_table(hgrms_ctx* h, size_t n, size_t tiles, bool per_image_k) {
     if (n > h->desc_cap) {
+        n = grown(n, h->desc_cap);
         if (h->d_desc) cudaFree(h->d_desc);
         if (h->host_desc) cudaFreeHost(h->host_desc);
         h->d_desc = nullptr;
@@ -384,6 +416,7 @@ int ensure_table(hgrms_ctx* h, size_t n, size_t tiles, bool per_image_k) {
         h->desc_cap = n;
     }
     if (tiles > h->tile_cap) {
+        tiles = grown(tiles, h->tile_cap);
         if (h->tile_img) cudaFree(h->tile_img);
         h->tile_img = nullptr;
         h->tile_cap = 0;
@@ -469,7 +502,8 @@ long long hybrid_bytes(const hg::FusedEntry* fe, int rows, int cols) {
 // with a width that is a multiple of 16, the image itself (the first fused
 // launch reads it directly; the box's rows and columns outside the image read
 // zeros).  They are rebuilt only when the layout changes and uploaded in
-// stream order, outside any captured graph.  Returns false when TMA cannot be
+// stream order from page-locked memory (an upload from pageable memory would
+// wait for the stream), outside any captured graph.  Returns false when TMA cannot be
 // used for this call (ordinary loads then); *user_ok is 1 when every image
 // the first launch reads in place has a map.
 bool ensure_tile_maps(hgrms_ctx* h, const hg::FusedEntry* fe, const BatchImg* im, int n, cudaStream_t s,
@@ -496,18 +530,30 @@ bool ensure_tile_maps(hgrms_ctx* h, const hg::FusedEntry* fe, const BatchImg* im
     }
     h->tmaps_key.clear();
     const size_t nm = (size_t)n * hg::kTmaMapsPerImage;
+    // The staging buffer may still be the source of the previous upload.
+    if (h->tmaps_ev && cudaEventSynchronize(h->tmaps_ev) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    if (!h->tmaps_ev && cudaEventCreateWithFlags(&h->tmaps_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
     if (nm > h->tmaps_cap) {
         if (h->tmaps) cudaFree(h->tmaps);
+        if (h->tmaps_host) cudaFreeHost(h->tmaps_host);
         h->tmaps = nullptr;
+        h->tmaps_host = nullptr;
         h->tmaps_cap = 0;
-        if (cudaMalloc(&h->tmaps, nm * sizeof(CUtensorMap)) != cudaSuccess) {
+        if (cudaMalloc(&h->tmaps, nm * sizeof(CUtensorMap)) != cudaSuccess ||
+            cudaMallocHost(&h->tmaps_host, nm * sizeof(CUtensorMap)) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
         h->tmaps_cap = nm;
     }
-    std::vector<CUtensorMap> maps(nm);
-    memset(maps.data(), 0, nm * sizeof(CUtensorMap));
+    CUtensorMap* maps = h->tmaps_host;
+    memset(maps, 0, nm * sizeof(CUtensorMap));
     int uok = 1;
     for (int i = 0; i < n; ++i) {
         const hg::ImgDesc& d = h->host_desc[i];
@@ -525,7 +571,8 @@ bool ensure_tile_maps(hgrms_ctx* h, const hg::FusedEntry* fe, const BatchImg* im
              encode_tile_map(&maps[(size_t)i * hg::kTmaMapsPerImage + 3], im[i].ptr, d.cols, d.rows, fe->SH);
         if (!ok) uok = 0;
     }
-    if (cudaMemcpyAsync(h->tmaps, maps.data(), nm * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s) != cudaSuccess) {
+    if (cudaMemcpyAsync(h->tmaps, maps, nm * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaEventRecord(h->tmaps_ev, s) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -1140,6 +1187,8 @@ HG_EXPORT void hgrms_destroy(hgrms_t h) {
         if (h->ctrl) cudaFree(h->ctrl);
         if (h->bar) cudaFree(h->bar);
         if (h->tmaps) cudaFree(h->tmaps);
+        if (h->tmaps_host) cudaFreeHost(h->tmaps_host);
+        if (h->tmaps_ev) cudaEventDestroy(h->tmaps_ev);
         if (h->chg_maps) cudaFree(h->chg_maps);
         if (h->lists) cudaFree(h->lists);
         if (h->bitmaps) cudaFree(h->bitmaps);
