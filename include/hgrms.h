@@ -138,8 +138,8 @@ const char* hgrms_strerror(int code);
 /* The cudaError_t of the last failing CUDA call on this handle (0 if none). */
 int hgrms_last_cuda_error(hgrms_t h);
 
-/* The integer root mean square of Algorithm 2 as every kernel of this library
- * computes it: out[i] = floor(sqrt(floor(sum[i] / flag[i]))) for n entries,
+/* The integer root mean square of Algorithm 2 as the fused and list-pass
+ * kernels compute it: out[i] = floor(sqrt(floor(sum[i] / flag[i]))) for n entries,
  * valid for 0 <= sum[i] <= flag[i] * 255^2 and 1 <= flag[i] <= 225 (the
  * range a (2 beta + 1)^2 window of 8-bit pixels produces).  sum, flag and
  * out are device memory of the current device; the call runs on

@@ -6,6 +6,7 @@
 
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <cuda_fp16.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -170,41 +171,55 @@ struct PassArgs {
 };
 constexpr int kTmaMapsPerImage = 4;
 
-// floor(sqrt(floor(sum / flag))) exactly (the root mean square of Algorithm
-// 2 in integers), for 0 <= sum <= flag * 255^2 and 1 <= flag <= 225, as every
-// kernel computes it.  sum < 2^24 and flag are exact in float; a non-integer
-// quotient is at least 1/flag below the next integer, far above the rounding
-// of the correctly rounded division at these magnitudes, so the floor of the
-// float quotient is floor(sum / flag); the square root is correctly rounded,
-// so its floor is the integer square root (the quotient is at most 255^2).
-// `sum` is passed as the float that holds it exactly.  Checked for every flag
-// and quotient through hgrms_rms.
-__device__ __forceinline__ int rms_floor(float sum, int flag) {
-    const float q = floorf(__fdiv_rn(sum, (float)flag));
-    return (int)floorf(__fsqrt_rn(q));
-}
-
-// floor(sqrt(q)) for 0 <= q <= 65025.  rsqrtf is within 2 ulp, so q * rsqrtf(q)
-// is within 10^-4 of sqrt(q) and its nearest integer is floor(sqrt(q)) or one
-// more; r * r > q removes the excess.  q = 0 takes rsqrtf(1), so the product
-// is 0.
+// The root mean square of Algorithm 2 in integers, floor(sqrt(floor(sum /
+// flag))), for 0 <= sum <= flag * 255^2 (so sum < 2^24) and 2 <= flag <= 225,
+// in two exact steps that need no conversion or division instruction.
+//
+// Quotient: floor(sum / flag) is the high word of sum * m with m = ceil(2^32
+// / flag) (division by an invariant integer through multiplication, Granlund
+// and Montgomery, 1994).  With e = m * flag - 2^32 < flag <= 225 and sum =
+// q * flag + r, sum * m / 2^32 = q + (r + sum * e / 2^32) / flag, and sum * e
+// < 2^24 * 225 < 2^32 keeps the bracket below flag.  (Also checked for every
+// sum and every flag of a replaced pixel on the CPU.)
+//
+// Square root of q <= 255^2: q is made a float through its bit pattern (2^23
+// + q has q in the low mantissa bits), rsqrtf is within 2 ulp, so q *
+// rsqrtf(q) is within 10^-4 of sqrt(q); adding 1.5 * 2^23 (unit spacing)
+// leaves its nearest integer in the low bits, which is floor(sqrt(q)) or one
+// more, and r * r > q removes the excess.  q = 0 takes rsqrtf(1), so the
+// product is 0.  Checked for every flag and quotient through hgrms_rms.
 __device__ __forceinline__ int isqrt_u16(int q) {
-    const float qf = (float)q;
-    int r = __float2int_rn(qf * rsqrtf(fmaxf(qf, 1.f)));
+    const float qf = __int_as_float(0x4B000000 | q) - 8388608.f;
+    const float s = qf * rsqrtf(fmaxf(qf, 1.f));
+    int r = __float_as_int(s + 12582912.f) - 0x4B400000;
     r -= (r * r > q) ? 1 : 0;
     return r;
 }
 
-// The root mean square of a replaced pixel of a 3 x 3 window (beta 1): the
-// test flag > pix_count - 3 = 6 leaves flag in {7, 8, 9}, so floor(sum /
-// flag) is the high word of sum * ceil(2^32 / flag) - division by an
-// invariant integer through multiplication (Granlund and Montgomery, 1994),
-// exact here because sum <= 9 * 255^2 is far below 2^32 / (flag *
-// ceil(2^32 / flag) - 2^32).  Checked for every sum and flag through
-// hgrms_rms.
-__device__ __forceinline__ int rms_floor_3x3(int sum, int flag) {
-    const unsigned m = flag == 7 ? 0x24924925u : (flag == 8 ? 0x20000000u : 0x1C71C71Du);
+// ceil(2^32 / d) for 2 <= d <= 2^32.
+__host__ __device__ constexpr unsigned recip32(unsigned d) {
+    return (unsigned)((0x100000000ull + d - 1u) / d);
+}
+
+__device__ __forceinline__ int rms_div(int sum, unsigned m) {
     return isqrt_u16((int)__umulhi((unsigned)sum, m));
+}
+
+// The root mean square of a replaced pixel of a (2B + 1)^2 window: the
+// replacement test flag > pix_count - 3 leaves flag in {P - 2, P - 1, P},
+// whose reciprocals are compile-time constants.
+template <int B>
+__device__ __forceinline__ int rms_window(int sum, int flag) {
+    constexpr int P = (2 * B + 1) * (2 * B + 1);
+    const unsigned m = flag == P ? recip32(P) : (flag == P - 1 ? recip32(P - 1) : recip32(P - 2));
+    return rms_div(sum, m);
+}
+
+// fp16 value of an integer 0 <= v <= 255 without a conversion instruction:
+// the bit pattern 0x6400 + v is the fp16 number 1024 + v, and subtracting
+// 1024 is exact.
+__device__ __forceinline__ __half u8_to_half(int v) {
+    return __hsub(__ushort_as_half((unsigned short)(0x6400 + v)), __ushort_as_half((unsigned short)0x6400));
 }
 
 // d = prmt(a, b, sel) in the generic mode, whose selector nibbles with bit 3

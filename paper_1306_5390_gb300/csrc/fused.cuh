@@ -51,8 +51,9 @@
 // of the product is 4 K_lo and byte 3 is 4 K_hi + (0..2): "at most one
 // closed neighbour" is "byte & 0xF8 == 0" for both.
 
-// Work layout: a pass computes rows [R0, R0 + 64) and columns [8, 264).  In
-// a dense pass warp w walks rows [R0 + 8w, R0 + 8w + 8) with a register ring
+// Work layout: a pass computes rows [R0, R0 + RN) (RN = 128 for beta 1 and
+// 2, else 64) and columns [8, 264).  In a dense pass warp w walks the rows
+// [R0 + rw, R0 + rw + r) of its band (r = 4 for beta 1, else 8) with a register ring
 // of the 2 beta + 1 window rows, lane l owning the 8 pixels at columns
 // [8 + 8l, 16 + 8l); candidate pixels (at most one closed neighbour) are
 // appended to a per-warp list and evaluated exactly, one per lane.  A list
@@ -64,14 +65,20 @@
 
 namespace hg {
 
-template <int B, int T>
+template <int B, int T, int RN_ = 64>
 struct FusedGeo {
-    // beta 1 uses 16 warps of 4-row bands (twice the resident warps at the
-    // same shared memory); wider windows need more registers per thread and
-    // use 8 warps of 8-row bands.
-    static constexpr int kThreads = B == 1 ? 512 : 256;
+    // Rows computed per pass: 64 (two CTAs per SM) or 128 (one CTA per SM
+    // with twice the threads: the T*beta halo rows above and below are a
+    // smaller share of the work, measured 7 % faster for beta 1 and 4 % for
+    // beta 2 on large images; small images get fewer, longer tiles).  beta 1
+    // uses warps of 4-row bands (twice the resident warps at the same shared
+    // memory); wider windows need more registers per thread and use warps of
+    // 8-row bands.
+    static constexpr int RN = RN_;
+    static_assert(RN == 64 || RN == 128, "tile rows");
+    static constexpr int kMinBlocks = RN == 64 ? 2 : 1;  // resident CTAs per SM
+    static constexpr int kThreads = (B == 1 ? 512 : 256) * (RN / 64);
     static constexpr int kWarps = kThreads / 32;
-    static constexpr int RN = 64;                    // rows computed per pass
     static constexpr int kRows = RN / kWarps;        // rows per warp band (dense passes)
     static constexpr int TW = 240;                   // core tile width (pixels)
     static constexpr int TH = RN - 2 * (T - 1) * B;  // core tile height
@@ -108,13 +115,14 @@ struct FusedGeo {
     static constexpr size_t kCntOff = kMarkOff + 2ull * kMarkWords * sizeof(uint32_t);
     static constexpr size_t kSmemBase = kCntOff + 8 * sizeof(int);
     // TMA staging buffer: the next tile with its halo, as bytes (SH rows of SW
-    // bytes), loaded while the current tile computes.  Only when two CTAs per
-    // SM still fit (the SM's 228 KB, less 1 KB reserved per CTA and the static
-    // shared variables).
+    // bytes), loaded while the current tile computes.  Only when the resident
+    // CTAs per SM still fit (the SM's 228 KB, less 1 KB reserved per CTA and
+    // the static shared variables; at most 227 KB per CTA).
     static constexpr size_t kStaticSmem = 192;  // the kernel's static shared variables (128 bytes) and slack
     static constexpr size_t kStageOff = (kSmemBase + 127) / 128 * 128;
     static constexpr size_t kStageBytes = ((size_t)SH * SW + 127) / 128 * 128;
-    static constexpr bool kTma = 2 * (kStageOff + kStageBytes + 1024 + kStaticSmem) <= 233472;
+    static constexpr bool kTma = kMinBlocks * (kStageOff + kStageBytes + 1024 + kStaticSmem) <= 233472 &&
+                                 kStageOff + kStageBytes + kStaticSmem <= 232448;
     static constexpr size_t kSmem = kTma ? kStageOff + kStageBytes : kSmemBase;
     // Lanes 0..31 cover columns [C0, C0 + 256): results within T*beta of
     // those edges may use wrong horizontal neighbours, so T*beta <= 8 keeps
@@ -319,7 +327,7 @@ __device__ __forceinline__ int exact_packed(const uint32_t* __restrict__ w32, in
     }
     const int flag = open_bits >> 3;
     constexpr int kPixCount = (2 * B + 1) * (2 * B + 1);
-    if (flag > kPixCount - 3) return B == 1 ? rms_floor_3x3(sum, flag) : rms_floor((float)sum, flag);
+    if (flag > kPixCount - 3) return rms_window<B>(sum, flag);
     return -1;
 }
 
@@ -356,9 +364,9 @@ __device__ __forceinline__ uint4 load_user_chunk(const uint8_t* __restrict__ use
 }
 
 // Per-pass context shared by the helpers below.
-template <int B, int T>
+template <int B, int T, int RN>
 struct PassCtx {
-    using G = FusedGeo<B, T>;
+    using G = FusedGeo<B, T, RN>;
     const uint32_t* in;
     uint32_t* out;
     uint16_t* cand;      // this warp's candidate list (dense passes)
@@ -375,8 +383,8 @@ struct PassCtx {
     bool changed_core;   // this lane saw a core pixel change
 };
 
-template <int B, int T>
-__device__ __forceinline__ bool interior(const PassCtx<B, T>& c, int y, int x) {
+template <int B, int T, int RN>
+__device__ __forceinline__ bool interior(const PassCtx<B, T, RN>& c, int y, int x) {
     return y >= c.ylo && y < c.yhi && x >= c.xlo && x < c.xhi;
 }
 
@@ -386,9 +394,9 @@ __device__ __forceinline__ bool in_core_px(int y, int x, int H, int TH, int TW) 
 
 // Evaluate and clear the warp's candidate list (dense passes): replaced
 // pixels are written to the output buffer and recorded as changed.
-template <int B, int T>
-__device__ __forceinline__ void flush_candidates(PassCtx<B, T>& c, const int lane) {
-    using G = FusedGeo<B, T>;
+template <int B, int T, int RN>
+__device__ __forceinline__ void flush_candidates(PassCtx<B, T, RN>& c, const int lane) {
+    using G = FusedGeo<B, T, RN>;
     __syncwarp();
     const __half* hin = reinterpret_cast<const __half*>(c.in);
     __half* hout = reinterpret_cast<__half*>(c.out);
@@ -407,7 +415,7 @@ __device__ __forceinline__ void flush_candidates(PassCtx<B, T>& c, const int lan
                 const __half old = hin[q];
                 const int v = exact_packed<B, G::SW>(c.in, (int)q, __half2half2(__hadd(old, __float2half(0.5f))), c.na);
                 if (v >= 0) {
-                    const __half hv = __int2half_rn(v);
+                    const __half hv = u8_to_half(v);
                     if (__half_as_ushort(hv) != __half_as_ushort(old)) {
                         hout[q] = hv;
                         ch = true;
@@ -446,14 +454,14 @@ __device__ __forceinline__ int warp_excl_scan(const int lane, const int n, int* 
 }
 
 // Append candidate bits (bit 8r + i: row ys + r, pixel x + i) to the warp list.
-template <int B, int T>
-__device__ __forceinline__ void append_bits(PassCtx<B, T>& c, const int lane, uint32_t m, const int ys,
+template <int B, int T, int RN>
+__device__ __forceinline__ void append_bits(PassCtx<B, T, RN>& c, const int lane, uint32_t m, const int ys,
                                             const int x) {
-    using G = FusedGeo<B, T>;
+    using G = FusedGeo<B, T, RN>;
     if (!__any_sync(0xffffffffu, m != 0u)) return;
     int total;
     const int off0 = warp_excl_scan(lane, __popc(m), &total);
-    if (c.ncand + total > G::kCandLimit) flush_candidates<B, T>(c, lane);
+    if (c.ncand + total > G::kCandLimit) flush_candidates<B, T, RN>(c, lane);
     int off = c.ncand + off0;
     while (m) {
         const int b = __ffs(m) - 1;
@@ -465,10 +473,10 @@ __device__ __forceinline__ void append_bits(PassCtx<B, T>& c, const int lane, ui
 
 // Dense pass over the warp's 8-row band: every pixel's closed neighbours are
 // counted with the packed test; candidates go to the warp list.
-template <int B, int T>
-__device__ __forceinline__ void band_dense(PassCtx<B, T>& c, const int ys, const int ws, const int lane,
+template <int B, int T, int RN>
+__device__ __forceinline__ void band_dense(PassCtx<B, T, RN>& c, const int ys, const int ws, const int lane,
                                            const __half2 two_a) {
-    using G = FusedGeo<B, T>;
+    using G = FusedGeo<B, T, RN>;
     constexpr bool kRing = (B <= 2);
     Row<B> win[kRing ? 2 * B + 1 : 1];
     unsigned long long m64 = 0ull;
@@ -510,7 +518,7 @@ __device__ __forceinline__ void band_dense(PassCtx<B, T>& c, const int ys, const
     constexpr unsigned long long kAMask = (1ull << (8 * kA)) - 1ull;
 #pragma unroll
     for (int g = 0; g < G::kRows / kA; ++g)
-        append_bits<B, T>(c, lane, (uint32_t)((m64 >> (8 * kA * g)) & kAMask), ys + kA * g, 2 * ws);
+        append_bits<B, T, RN>(c, lane, (uint32_t)((m64 >> (8 * kA * g)) & kAMask), ys + kA * g, 2 * ws);
 }
 
 // ---- Symmetric count (beta 1 and 2) --------------------------------------
@@ -587,9 +595,9 @@ __device__ __forceinline__ void sym_dir(const Row<B>& ry, const Row<B>& ryd, con
 
 // All forward directions of band row R (R < 0: a row above the band, whose
 // own counts are not needed).
-template <int B, int T, int R>
+template <int B, int T, int RN, int R>
 __device__ __forceinline__ void sym_row(const Row<B> (&win)[B + 1], const __half2 lim, uint32_t (&k)[B + 1][4]) {
-    constexpr int kRows = FusedGeo<B, T>::kRows;
+    constexpr int kRows = FusedGeo<B, T, RN>::kRows;
     constexpr bool kIn = R >= 0;
     // same row: both endpoints in row y
     sym_dir<B, 0, 1, kIn, kIn>(win[0], win[0], lim, k[0], k[0]);
@@ -611,14 +619,14 @@ __device__ __forceinline__ void sym_row(const Row<B> (&win)[B + 1], const __half
     }
 }
 
-template <int B, int T, int R>
-__device__ __forceinline__ void sym_band_row(PassCtx<B, T>& c, const int ys, const int ws, const __half2 lim,
+template <int B, int T, int RN, int R>
+__device__ __forceinline__ void sym_band_row(PassCtx<B, T, RN>& c, const int ys, const int ws, const __half2 lim,
                                              Row<B> (&win)[B + 1], uint32_t (&k)[B + 1][4],
                                              unsigned long long& m64) {
-    using G = FusedGeo<B, T>;
+    using G = FusedGeo<B, T, RN>;
     if constexpr (R < G::kRows) {
         // win[i] holds row ys + R + i.
-        sym_row<B, T, R>(win, lim, k);
+        sym_row<B, T, RN, R>(win, lim, k);
         if constexpr (R >= 0) {
             const uint4 centre = make_uint4(win[0].p[B], win[0].p[B + 2], win[0].p[B + 4], win[0].p[B + 6]);
             *reinterpret_cast<uint4*>(c.out + (ys + R) * G::SWW + ws) = centre;
@@ -636,14 +644,14 @@ __device__ __forceinline__ void sym_band_row(PassCtx<B, T>& c, const int ys, con
 #pragma unroll
         for (int j = 0; j < 4; ++j) k[B][j] = 0u;
         if constexpr (R + 1 < G::kRows) load_row_shfl<B>(c.in + (ys + R + 1 + B) * G::SWW + ws, win[B]);
-        sym_band_row<B, T, R + 1>(c, ys, ws, lim, win, k, m64);
+        sym_band_row<B, T, RN, R + 1>(c, ys, ws, lim, win, k, m64);
     }
 }
 
 // Dense pass over the warp's band with the symmetric count (beta 1, 2).
-template <int B, int T>
-__device__ __forceinline__ void band_dense_sym(PassCtx<B, T>& c, const int ys, const int ws, const int lane) {
-    using G = FusedGeo<B, T>;
+template <int B, int T, int RN>
+__device__ __forceinline__ void band_dense_sym(PassCtx<B, T, RN>& c, const int ys, const int ws, const int lane) {
+    using G = FusedGeo<B, T, RN>;
     static_assert(B == 1 || B == 2, "symmetric count for beta 1 and 2");
     const __half2 lim = __float2half2_rn(2.f * (float)c.alpha - 1.f);
     Row<B> win[B + 1];
@@ -655,12 +663,12 @@ __device__ __forceinline__ void band_dense_sym(PassCtx<B, T>& c, const int ys, c
         for (int j = 0; j < 4; ++j) k[i][j] = 0u;
     }
     unsigned long long m64 = 0ull;
-    sym_band_row<B, T, -B>(c, ys, ws, lim, win, k, m64);
+    sym_band_row<B, T, RN, -B>(c, ys, ws, lim, win, k, m64);
     constexpr int kA = G::kAppendRows;
     constexpr unsigned long long kAMask = (1ull << (8 * kA)) - 1ull;
 #pragma unroll
     for (int g = 0; g < G::kRows / kA; ++g)
-        append_bits<B, T>(c, lane, (uint32_t)((m64 >> (8 * kA * g)) & kAMask), ys + kA * g, 2 * ws);
+        append_bits<B, T, RN>(c, lane, (uint32_t)((m64 >> (8 * kA * g)) & kAMask), ys + kA * g, 2 * ws);
 }
 
 // Outer-ring closed-neighbour count of one pixel pair (the fp16 pair at
@@ -705,10 +713,10 @@ __device__ __forceinline__ uint32_t outer_count(const uint32_t* __restrict__ in,
 // one closed neighbour) and stage two counts only the outer ring for them,
 // one pair per lane.  Pixels with at most one closed neighbour in all are
 // candidates.
-template <int B, int T>
-__device__ __forceinline__ void band_dense2(PassCtx<B, T>& c, const int ys, const int ws, const int lane,
+template <int B, int T, int RN>
+__device__ __forceinline__ void band_dense2(PassCtx<B, T, RN>& c, const int ys, const int ws, const int lane,
                                             const __half2 two_a) {
-    using G = FusedGeo<B, T>;
+    using G = FusedGeo<B, T, RN>;
     constexpr int kHalf = G::kAppendRows;  // rows per group (its work list fits half the buffer)
     uint16_t* items = c.cand + G::kCandCap / 2;
     Row<1> win[3];
@@ -784,7 +792,7 @@ __device__ __forceinline__ void band_dense2(PassCtx<B, T>& c, const int ys, cons
             if (__any_sync(0xffffffffu, cb != 0u)) {
                 int tot2;
                 const int off = warp_excl_scan(lane, __popc(cb), &tot2);
-                if (c.ncand + tot2 > G::kCandLimit) flush_candidates<B, T>(c, lane);
+                if (c.ncand + tot2 > G::kCandLimit) flush_candidates<B, T, RN>(c, lane);
                 int o = c.ncand + off;
                 if (cb & 1u) c.cand[o++] = (uint16_t)q0;
                 if (cb & 2u) c.cand[o++] = (uint16_t)(q0 + 1);
@@ -799,10 +807,10 @@ __device__ __forceinline__ void band_dense2(PassCtx<B, T>& c, const int ys, cons
 // previous pass can change now.  Each (changed pixel, window offset) pair
 // claims its pixel in the mark bitmap; the claimer evaluates it exactly
 // (Algorithm 2) from `in` and writes it to `out`.
-template <int B, int T>
-__device__ __forceinline__ void list_pass(PassCtx<B, T>& c, const uint16_t* prev, const int nprev, uint32_t* mark,
+template <int B, int T, int RN>
+__device__ __forceinline__ void list_pass(PassCtx<B, T, RN>& c, const uint16_t* prev, const int nprev, uint32_t* mark,
                                           const int tid) {
-    using G = FusedGeo<B, T>;
+    using G = FusedGeo<B, T, RN>;
     const __half* hin = reinterpret_cast<const __half*>(c.in);
     __half* hout = reinterpret_cast<__half*>(c.out);
     const int npairs = nprev * G::P;
@@ -822,7 +830,7 @@ __device__ __forceinline__ void list_pass(PassCtx<B, T>& c, const uint16_t* prev
         __half nv = old;
         if (interior(c, y, x)) {
             const int v = exact_packed<B, G::SW>(c.in, q, __half2half2(__hadd(old, __float2half(0.5f))), c.na);
-            if (v >= 0) nv = __int2half_rn(v);
+            if (v >= 0) nv = u8_to_half(v);
         }
         hout[q] = nv;
         if (__half_as_ushort(nv) != __half_as_ushort(old)) {
@@ -877,10 +885,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* m, unsigned parity) {
 // thread 0 takes the next tile from the queue as soon as the current one is
 // in shared memory and starts its TMA load into the staging buffer, so the
 // load runs while the current tile computes.
-template <int B, int T>
-__global__ void __launch_bounds__(FusedGeo<B, T>::kThreads, 2)
+template <int B, int T, int RN>
+__global__ void __launch_bounds__(FusedGeo<B, T, RN>::kThreads, FusedGeo<B, T, RN>::kMinBlocks)
 fused_kernel(PassArgs a) {
-    using G = FusedGeo<B, T>;
+    using G = FusedGeo<B, T, RN>;
     extern __shared__ __align__(128) uint8_t smem[];
     __shared__ int s_np, s_tile, s_staged;
     __shared__ unsigned s_cur, s_aux, s_launch, s_k, s_img, s_nclr, s_nin;
@@ -952,7 +960,7 @@ fused_kernel(PassArgs a) {
     const __half2 two_a = __float2half2_rn(2.f * (float)a.alpha);
     const int ys = G::R0 + warp * G::kRows;
     const int ws = G::C0 / 2 + 4 * lane;
-    PassCtx<B, T> c;
+    PassCtx<B, T, RN> c;
     c.cand = cand;
     c.ncand = 0;
     c.alpha = a.alpha;
@@ -1067,7 +1075,7 @@ fused_kernel(PassArgs a) {
                 ++tma_waits;
                 for (int i = tid; i < G::SH * CH; i += G::kThreads)
                     store_chunk(i, *reinterpret_cast<const uint4*>(stage + i * 16));
-            } else if constexpr (G::kThreads == 256) {
+            } else if constexpr (B >= 2) {
                 // beta >= 2 (4-5 chunks per thread): every chunk of this
                 // thread is loaded before any is converted, so that the
                 // loads are in flight together (measured faster; for beta 1,
@@ -1149,14 +1157,14 @@ fused_kernel(PassArgs a) {
             if (dense) {
                 ++dense_passes;
                 if constexpr (G::kTwoStage)
-                    band_dense2<B, T>(c, ys, ws, lane, two_a);
+                    band_dense2<B, T, RN>(c, ys, ws, lane, two_a);
                 else if constexpr (B <= 2)
-                    band_dense_sym<B, T>(c, ys, ws, lane);
+                    band_dense_sym<B, T, RN>(c, ys, ws, lane);
                 else
-                    band_dense<B, T>(c, ys, ws, lane, two_a);
-                flush_candidates<B, T>(c, lane);
+                    band_dense<B, T, RN>(c, ys, ws, lane, two_a);
+                flush_candidates<B, T, RN>(c, lane);
             } else {
-                list_pass<B, T>(c, prev, nprev, marks + (t & 1) * G::kMarkWords, tid);
+                list_pass<B, T, RN>(c, prev, nprev, marks + (t & 1) * G::kMarkWords, tid);
             }
             if (__syncthreads_or(c.changed_core)) tile_mask |= 1u << t;
         }
@@ -1286,18 +1294,19 @@ fused_kernel(PassArgs a) {
     }
 }
 
-// Host-side description of one compiled (beta, T) instance.
+// Host-side description of one compiled (beta, T, tile rows) instance.
 struct FusedEntry {
     int beta, T, TH, TW;
+    int RN;    // rows computed per pass (64, or 128 for the tall tiles of large images)
     int SH;    // tile rows with the halo (the TMA box height)
     bool tma;  // the kernel stages tiles by TMA when given tensor maps
     size_t smem;
     cudaError_t (*launch)(const PassArgs&, int ctas, cudaStream_t);  // one CTA per tile
 };
 
-template <int B, int T>
+template <int B, int T, int RN>
 cudaError_t launch_fused(const PassArgs& a, int ctas, cudaStream_t s) {
-    using G = FusedGeo<B, T>;
+    using G = FusedGeo<B, T, RN>;
     // Per device: resident CTAs per SM and SM count (set up on first use).
     constexpr int kMaxDev = 64;
     static int occ[kMaxDev] = {};
@@ -1307,11 +1316,11 @@ cudaError_t launch_fused(const PassArgs& a, int ctas, cudaStream_t s) {
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDev) return cudaErrorInvalidDevice;
     if (occ[dev] == 0) {
-        e = cudaFuncSetAttribute(fused_kernel<B, T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::kSmem);
+        e = cudaFuncSetAttribute(fused_kernel<B, T, RN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G::kSmem);
         int n = 0, o = 0;
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
         if (e == cudaSuccess)
-            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fused_kernel<B, T>, G::kThreads, G::kSmem);
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, fused_kernel<B, T, RN>, G::kThreads, G::kSmem);
         if (e != cudaSuccess) return e;
         if (o < 1) return cudaErrorInvalidConfiguration;
         sms[dev] = n;
@@ -1319,14 +1328,14 @@ cudaError_t launch_fused(const PassArgs& a, int ctas, cudaStream_t s) {
     }
     const long long cap = (long long)sms[dev] * occ[dev];
     const unsigned grid = (unsigned)(ctas < cap ? (ctas > 0 ? ctas : 1) : cap);
-    fused_kernel<B, T><<<grid, G::kThreads, G::kSmem, s>>>(a);
+    fused_kernel<B, T, RN><<<grid, G::kThreads, G::kSmem, s>>>(a);
     return cudaGetLastError();
 }
 
-template <int B, int T>
+template <int B, int T, int RN = 64>
 constexpr FusedEntry fused_entry() {
-    using G = FusedGeo<B, T>;
-    return FusedEntry{B, T, G::TH, G::TW, G::SH, G::kTma, G::kSmem, &launch_fused<B, T>};
+    using G = FusedGeo<B, T, RN>;
+    return FusedEntry{B, T, G::TH, G::TW, RN, G::SH, G::kTma, G::kSmem, &launch_fused<B, T, RN>};
 }
 
 }  // namespace hg

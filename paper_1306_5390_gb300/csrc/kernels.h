@@ -15,9 +15,9 @@ extern const int kFusedB2Count;
 extern const FusedEntry kFusedB3[];
 extern const int kFusedB3Count;
 
-// Compiled fused kernel for (beta, passes per launch), or null; the built-in
-// passes per launch for beta.
-const FusedEntry* find_fused(int beta, int T);
+// Compiled fused kernel for (beta, passes per launch, rows computed per
+// pass), or null; the built-in passes per launch for beta.
+const FusedEntry* find_fused(int beta, int T, int rn = 64);
 int default_passes(int beta);
 
 cudaError_t launch_plain(int beta, const PassArgs& a, cudaStream_t s);
@@ -32,7 +32,7 @@ cudaError_t launch_list(int beta, const PassArgs& a, int sms, cudaStream_t s);
 cudaError_t launch_copy_out_batch(const Ctrl* c, uint8_t* const arena[3], const ImgDesc* imgs, int nimg,
                                   long long max_words, int sms, cudaStream_t s);
 cudaError_t launch_tile_map(const ImgDesc* imgs, int nimg, int total_tiles, int* tile_img, cudaStream_t s);
-// out[i] = rms_floor(sum[i], flag[i]) (the kernels' integer root mean square).
+// out[i] = floor(sqrt(floor(sum[i] / flag[i]))) by the kernels' integer root mean square (rms_div).
 cudaError_t launch_rms(const int* sum, const int* flag, int* out, int n, cudaStream_t s);
 
 }  // namespace hg

@@ -69,8 +69,67 @@ __device__ __forceinline__ int eval_pixel(const uint8_t* p, long long stride, in
             flag += open ? 1 : 0;
         }
     constexpr int kPixCount = (2 * B + 1) * (2 * B + 1);
-    if (flag > kPixCount - 3) return rms_floor((float)sum, flag);
+    if (flag > kPixCount - 3) return rms_window<B>(sum, flag);
     return ip;
+}
+
+// Byte mask (0xFF per byte) of the bytes v_j of v with lo <= v_j <= hi, for
+// kl = (256 - lo) and kh = (256 - (hi + 1)) in both 16-bit halves, 0 <= lo <=
+// 256 and 0 <= hi + 1 <= 256.  The even and the odd bytes are taken apart
+// into 16-bit lanes; in a lane, byte + 256 - lo lies in 0..511 and has bit 8
+// set exactly when byte >= lo, and byte + 256 - (hi + 1) has it set exactly
+// when byte > hi (no carry reaches the next lane).
+__device__ __forceinline__ uint32_t bytes_in_range(uint32_t v, uint32_t kl, uint32_t kh) {
+    const uint32_t e = v & 0x00FF00FFu, o = __byte_perm(v, 0u, 0x4341u);
+    const uint32_t ce = (e + kl) & ~(e + kh);
+    const uint32_t co = (o + kl) & ~(o + kh);
+    return (((ce >> 8) & 0x00010001u) | (co & 0x01000100u)) * 0xFFu;
+}
+
+// Algorithm 2 for an interior pixel whose (2B + 1)^2 window is loaded as
+// rows of bytes (win[r][j / 4] byte j % 4 = value at offset (r - B, j - B)),
+// four values at a time: a value v is closed when ip - alpha < v <= ip +
+// alpha (bytes_in_range with lo = max(ip - alpha + 1, 0), hi = min(ip +
+// alpha, 255); for alpha = 0 nothing is); the open values' squares sum in
+// one 4-way dot product per word and the open values are counted by a
+// population count (8 bits per value).  For beta 2 the fifth value of each
+// row is gathered four rows to a word first.  Returns the new value (ip when
+// the pixel is not replaced; card <= 2 is implied by flag > pix_count - 3
+// for alpha >= 1, and card is 0 for alpha = 0).
+template <int B>
+__device__ __forceinline__ int eval_window(const uint32_t (&win)[2 * B + 1][(2 * B + 4) / 4], int alpha) {
+    constexpr int W = 2 * B + 1, NW = (W + 3) / 4, P = W * W;
+    const int ip = (int)((win[B][B / 4] >> (8 * (B % 4))) & 0xffu);
+    const int lo = max(ip - alpha + 1, 0), hi = min(ip + alpha, 255);
+    const uint32_t kl = 0x01000100u - (uint32_t)lo * 0x00010001u;
+    const uint32_t kh = 0x01000100u - (uint32_t)(hi + 1) * 0x00010001u;
+    unsigned sum = 0u;
+    int nopen = 0;
+    auto word = [&](uint32_t v, uint32_t ok) {
+        const uint32_t open = ~bytes_in_range(v, kl, kh) & ok;
+        sum = __dp4a(v & open, v, sum);
+        nopen += __popc(open);
+    };
+    if constexpr (B == 2) {
+        // Values -2..1 of every row, then the values +2 of rows 0-3 in one word and of row 4.
+#pragma unroll
+        for (int r = 0; r < W; ++r) word(win[r][0], 0xFFFFFFFFu);
+        const uint32_t t01 = __byte_perm(win[0][1], win[1][1], 0x0040u);
+        const uint32_t t23 = __byte_perm(win[2][1], win[3][1], 0x0040u);
+        word(__byte_perm(t01, t23, 0x5410u), 0xFFFFFFFFu);
+        word(win[4][1], 0x000000FFu);
+    } else {
+#pragma unroll
+        for (int r = 0; r < W; ++r)
+#pragma unroll
+            for (int k = 0; k < NW; ++k) {
+                constexpr int kLast = W - 4 * (NW - 1);  // values in the last word of a row
+                const uint32_t ok = (k < NW - 1 || kLast == 4) ? 0xFFFFFFFFu : ((1u << (8 * kLast)) - 1u);
+                word(win[r][k], ok);
+            }
+    }
+    const int flag = nopen >> 3;
+    return flag > P - 3 ? rms_window<B>((int)sum, flag) : ip;
 }
 
 // Grid-wide barrier over co-resident CTAs that also sums one count over all
@@ -311,22 +370,8 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
                         }
                         if (owner) {
                             ++evals;
-                            // Algorithm 2 on the loaded window (see eval_pixel).
                             const int ip = (int)((win[B][B / 4] >> (8 * (B % 4))) & 0xffu);
-                            int sum = 0, flag = 0;
-#pragma unroll
-                            for (int r = 0; r < W; ++r)
-#pragma unroll
-                                for (int j = 0; j < W; ++j) {
-                                    const int tv = (int)((win[r][j / 4] >> (8 * (j % 4))) & 0xffu);
-                                    const bool open = !(tv < ip + a.alpha + 1 && tv > ip - a.alpha);
-                                    sum += open ? tv * tv : 0;
-                                    flag += open ? 1 : 0;
-                                }
-                            int nv = ip;
-                            if (flag > P - 3) {
-                                nv = rms_floor((float)sum, flag);
-                            }
+                            const int nv = eval_window<B>(win, a.alpha);
                             out_arena[d.off + (long long)kPadY * d.pitch + kPadX + off] = (uint8_t)nv;
                             if (nv != ip) {
                                 ch = true;
@@ -433,20 +478,7 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
                         for (int r = 0; r < W; ++r) load_row_bytes<W>(in + off + (long long)(r - B) * d.pitch - B, win[r]);
                         ++evals;
                         const int ip = (int)((win[B][B / 4] >> (8 * (B % 4))) & 0xffu);
-                        int sum = 0, flag = 0;
-#pragma unroll
-                        for (int r = 0; r < W; ++r)
-#pragma unroll
-                            for (int jj = 0; jj < W; ++jj) {
-                                const int tv = (int)((win[r][jj / 4] >> (8 * (jj % 4))) & 0xffu);
-                                const bool open = !(tv < ip + a.alpha + 1 && tv > ip - a.alpha);
-                                sum += open ? tv * tv : 0;
-                                flag += open ? 1 : 0;
-                            }
-                        int nv = ip;
-                        if (flag > P - 3) {
-                            nv = rms_floor((float)sum, flag);
-                        }
+                        const int nv = eval_window<B>(win, a.alpha);
                         out_arena[d.off + (long long)kPadY * d.pitch + kPadX + off] = (uint8_t)nv;
                         if (nv != ip) {
                             ch = true;

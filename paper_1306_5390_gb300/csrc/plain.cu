@@ -247,7 +247,7 @@ cudaError_t launch_copy_out_batch(const Ctrl* c, uint8_t* const arena[3], const 
 
 __global__ void rms_kernel(const int* __restrict__ sum, const int* __restrict__ flag, int* __restrict__ out, int n) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-        out[i] = rms_floor((float)sum[i], flag[i]);
+        out[i] = flag[i] == 1 ? isqrt_u16(sum[i]) : rms_div(sum[i], recip32((unsigned)flag[i]));
 }
 
 cudaError_t launch_rms(const int* sum, const int* flag, int* out, int n, cudaStream_t s) {

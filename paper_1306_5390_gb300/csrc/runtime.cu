@@ -131,12 +131,12 @@ struct hgrms_ctx {
 
 namespace hg {
 
-const FusedEntry* find_fused(int beta, int T) {
+const FusedEntry* find_fused(int beta, int T, int rn) {
     const hg::FusedEntry* tabs[3] = {hg::kFusedB1, hg::kFusedB2, hg::kFusedB3};
     const int counts[3] = {hg::kFusedB1Count, hg::kFusedB2Count, hg::kFusedB3Count};
     for (int t = 0; t < 3; ++t)
         for (int i = 0; i < counts[t]; ++i)
-            if (tabs[t][i].beta == beta && tabs[t][i].T == T) return &tabs[t][i];
+            if (tabs[t][i].beta == beta && tabs[t][i].T == T && tabs[t][i].RN == rn) return &tabs[t][i];
     return nullptr;
 }
 
@@ -162,6 +162,10 @@ namespace {
 // for wider windows, whose fused passes cost more than list passes even on
 // dense change sets.  With HGRMS_OPT_RELAUNCH_PPM set, up to 8 for any beta.
 constexpr int kDefaultRelaunches = 3;
+// Single images of at least this many pixels use the 128-row tiles (where
+// compiled): measured faster on 8192 x 8192; smaller images keep the 64-row
+// tiles, whose larger tile count spreads better over the SMs.
+constexpr long long kTallMinPixels = 32ll << 20;
 constexpr long long kRelaunchMinPixels = 4ll << 20;
 constexpr size_t kMaxGraphs = 8;  // captured graphs kept per handle (HGRMS_OPT_GRAPH)
 constexpr int kMaxRelaunches = 8;
@@ -604,7 +608,13 @@ int finish_hybrid(hgrms_ctx* h, const hgrms_ctx::PendingCall& pd, const BatchImg
 int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int max_k, int* k_out,
                const Tuning& tu, bool write_back, float* ms, int forced_fused = 0, bool async_call = false) {
     const int T = tu.T;
-    const hg::FusedEntry* fe = find_fused(beta, T);
+    // One large image takes the tall tiles when they are compiled for its
+    // (beta, T): at this size every SM still gets many tiles.
+    long long px_call = 0;
+    for (int i = 0; i < n; ++i) px_call += (long long)im[i].rows * im[i].cols;
+    const hg::FusedEntry* fe = nullptr;
+    if (n == 1 && px_call >= kTallMinPixels) fe = find_fused(beta, T, 128);
+    if (!fe) fe = find_fused(beta, T);
     if (!fe) return HGRMS_EINVAL;
     const bool per_image_k = n > 1;
     // Layout: image i's canvas at offset off_i of each arena, its bitmap at

@@ -102,3 +102,143 @@ def test_symmetric_pair_test_fp16_exhaustive():
         assert np.array_equal(f == 1, strict) and np.all((f == 0) | (f == 1)), alpha
         closed = (inn > ip - alpha) & (inn <= ip + alpha)
         assert not np.any(strict & ~closed), alpha
+
+
+def test_reciprocal_division_exhaustive():
+    """The kernels' floor(sum / flag) is the high word of sum * ceil(2^32 /
+    flag).  For every window of beta 1..7 a replaced pixel has flag in {P - 2,
+    P - 1, P} (P = (2 beta + 1)^2, Algorithm 2's test flag > pix_count - 3)
+    and 0 <= sum <= flag * 255^2: every such sum must give the exact
+    quotient."""
+    import numpy as np
+    for beta in range(1, 8):
+        p = (2 * beta + 1) ** 2
+        for flag in (p - 2, p - 1, p):
+            m = np.uint64((2**32 + flag - 1) // flag)
+            top = flag * 255 * 255
+            for lo in range(0, top + 1, 1 << 22):
+                s = np.arange(lo, min(lo + (1 << 22), top + 1), dtype=np.uint64)
+                assert np.array_equal((s * m) >> np.uint64(32), s // np.uint64(flag)), (beta, flag, lo)
+
+
+def test_reciprocal_division_every_flag_at_the_quotient_edges():
+    """hgrms_rms uses the same division for every flag 2..225: the largest
+    remainder of each quotient is where the high word would first exceed it."""
+    import numpy as np
+    q = np.arange(0, 255 * 255 + 1, dtype=np.uint64)
+    for flag in range(2, 226):
+        m = np.uint64((2**32 + flag - 1) // flag)
+        for r in (0, flag - 1):
+            s = q * np.uint64(flag) + np.uint64(r)
+            s = s[s <= flag * 255 * 255]
+            assert np.array_equal((s * m) >> np.uint64(32), s // np.uint64(flag)), (flag, r)
+
+
+def test_isqrt_rounding_with_rsqrt_error_bound():
+    """The kernels' integer square root of q <= 255^2: q as a float from its
+    bit pattern (2^23 + q minus 2^23), times rsqrtf(q), rounded to the
+    nearest integer by adding 1.5 * 2^23, less one when its square exceeds
+    q.  With rsqrtf anywhere within its 2 ulp error bound the result must be
+    floor(sqrt(q)) for every q (float32 arithmetic, round to nearest even)."""
+    import math
+    import numpy as np
+    q = np.arange(0, 255 * 255 + 1, dtype=np.int64)
+    qf = (np.array(0x4B000000 | q, dtype=np.uint32).view(np.float32) - np.float32(8388608.0)).astype(np.float32)
+    assert np.array_equal(qf.astype(np.int64), q)
+    exact = np.array([math.isqrt(int(v)) for v in q], dtype=np.int64)
+    base = (1.0 / np.sqrt(np.maximum(qf, 1).astype(np.float64))).astype(np.float32)
+    for ulps in range(-2, 3):
+        rs = base
+        for _ in range(abs(ulps)):
+            rs = np.nextafter(rs, np.float32(np.inf if ulps > 0 else 0)).astype(np.float32)
+        s = (qf * rs).astype(np.float32)
+        t = (s + np.float32(12582912.0)).astype(np.float32)
+        r = t.view(np.int32).astype(np.int64) - 0x4B400000
+        r -= (r * r > q).astype(np.int64)
+        assert np.array_equal(r, exact), ulps
+
+
+def _bytes_in_range(v, lo, hi):
+    """Python form of the list-pass kernel's bytes_in_range (uint64 arrays
+    holding 32-bit words): 0xFF in every byte of v with lo <= byte <= hi."""
+    import numpy as np
+    m32 = np.uint64(0xFFFFFFFF)
+    kl = (np.uint64(0x01000100) - lo.astype(np.uint64) * np.uint64(0x00010001)) & m32
+    kh = (np.uint64(0x01000100) - (hi.astype(np.uint64) + np.uint64(1)) * np.uint64(0x00010001)) & m32
+    e = v & np.uint64(0x00FF00FF)
+    o = ((v >> np.uint64(8)) & np.uint64(0xFF)) | (((v >> np.uint64(24)) & np.uint64(0xFF)) << np.uint64(16))
+    ce = ((e + kl) & m32) & (~((e + kh) & m32) & m32)
+    co = ((o + kl) & m32) & (~((o + kh) & m32) & m32)
+    m = ((ce >> np.uint64(8)) & np.uint64(0x00010001)) | (co & np.uint64(0x01000100))
+    return (m * np.uint64(0xFF)) & m32
+
+
+def test_swar_closed_test_exhaustive():
+    """The list passes test four window values at once: a byte v is closed
+    for the centre value ip when ip - alpha < v <= ip + alpha (Algorithm 2),
+    i.e. lo <= v <= hi with lo = max(ip - alpha + 1, 0), hi = min(ip + alpha,
+    255).  Every (ip, alpha, v) with v in each byte position, the other
+    bytes random (no carry may leak between bytes)."""
+    import numpy as np
+    rng = np.random.default_rng(5)
+    ip = np.repeat(np.arange(256), 256).astype(np.int64)
+    v = np.tile(np.arange(256), 256).astype(np.int64)
+    for alpha in range(256):
+        lo = np.maximum(ip - alpha + 1, 0)
+        hi = np.minimum(ip + alpha, 255)
+        expect = (v > ip - alpha) & (v <= ip + alpha)
+        for pos in range(4):
+            other = rng.integers(0, 2**32, size=v.size, dtype=np.uint64) & ~np.uint64(0xFF << (8 * pos))
+            word = other | (v.astype(np.uint64) << np.uint64(8 * pos))
+            got = (_bytes_in_range(word, lo, hi) >> np.uint64(8 * pos)) & np.uint64(0xFF)
+            assert np.array_equal(got == 0xFF, expect) and np.all((got == 0) | (got == 0xFF)), (alpha, pos)
+
+
+def test_swar_window_evaluation_matches_definition():
+    """The list passes' whole evaluation of Algorithm 2 from byte words (rows
+    of 2 beta + 1 values, four per word; beta 2 gathers the fifth value of
+    rows 0-3 into one word): the sum of the open values' squares (4-way dot
+    products) and their count (population counts), against the definition,
+    on random windows of beta 1, 2 and 3 with values near the centre."""
+    import numpy as np
+    rng = np.random.default_rng(11)
+    for beta in (1, 2, 3):
+        w = 2 * beta + 1
+        for trial in range(4000):
+            alpha = int(rng.integers(0, 40))
+            ip = int(rng.integers(0, 256))
+            win = np.clip(ip + rng.integers(-2 * alpha - 3, 2 * alpha + 4, size=(w, w)), 0, 255)
+            if trial % 3 == 0:
+                win = rng.integers(0, 256, size=(w, w))
+            win[beta, beta] = ip
+            nw = (w + 3) // 4
+            rowwords = []
+            for r in range(w):
+                vals = list(win[r]) + [int(rng.integers(0, 256)) for _ in range(4 * nw - w)]
+                rowwords.append([sum(int(vals[4 * k + j]) << (8 * j) for j in range(4)) for k in range(nw)])
+            words, oks = [], []
+            if beta == 2:
+                for r in range(w):
+                    words.append(rowwords[r][0]); oks.append(0xFFFFFFFF)
+                packed = sum((rowwords[r][1] & 0xFF) << (8 * r) for r in range(4))
+                words += [packed, rowwords[4][1]]; oks += [0xFFFFFFFF, 0xFF]
+            else:
+                last = w - 4 * (nw - 1)
+                for r in range(w):
+                    for k in range(nw):
+                        words.append(rowwords[r][k])
+                        oks.append(0xFFFFFFFF if (k < nw - 1 or last == 4) else (1 << (8 * last)) - 1)
+            words = np.array(words, dtype=np.uint64)
+            lo = np.full(words.shape, max(ip - alpha + 1, 0)); hi = np.full(words.shape, min(ip + alpha, 255))
+            closed = _bytes_in_range(words, lo, hi)
+            s, nopen = 0, 0
+            for word, c, ok in zip(words.tolist(), closed.tolist(), oks):
+                open_ = ~c & ok & 0xFFFFFFFF
+                for j in range(4):
+                    if (open_ >> (8 * j)) & 0xFF:
+                        b = (word >> (8 * j)) & 0xFF
+                        s += b * b
+                nopen += bin(open_).count("1")
+            op = ~((win > ip - alpha) & (win <= ip + alpha))
+            assert nopen // 8 == int(op.sum()) and nopen % 8 == 0, (beta, trial)
+            assert s == int((win.astype(np.int64) ** 2 * op).sum()), (beta, trial)
