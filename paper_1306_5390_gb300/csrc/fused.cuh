@@ -286,8 +286,8 @@ __device__ __forceinline__ uint32_t candidate_mask(const uint32_t na, const uint
 //    = 0 every value is open, the pixel itself included.
 //  * Values as bytes: the fp16 number 1024 + v has v as its low byte.
 //  * With four values and their masks in one word each, the open values'
-//    squares sum in one 4-way integer dot product, and the open values are
-//    counted by a population count (8 bits per value).
+//    squares sum in one 4-way integer dot product, and a second one with
+//    0x01010101 counts the open values (255 per open value).
 template <int B, int SW>
 __device__ __forceinline__ int exact_packed(const uint32_t* __restrict__ w32, int q, __half2 cp, __half2 na) {
     constexpr int SWW = SW / 2;
@@ -302,7 +302,7 @@ __device__ __forceinline__ int exact_packed(const uint32_t* __restrict__ w32, in
     const uint32_t first_ok = odd ? 0xFFFFFF00u : 0xFFFFFFFFu;
     const uint32_t last_ok = odd ? kLastPad : (kLastPad >> 8);
     const __half2 k1024 = __float2half2_rn(1024.f);
-    int sum = 0, open_bits = 0;
+    int sum = 0, open255 = 0;  // sum of the open values' squares; 255 per open value
 #pragma unroll
     for (int dy = -B; dy <= B; ++dy) {
         const uint32_t* row = w32 + (h0 >> 1) + dy * SWW;
@@ -322,13 +322,15 @@ __device__ __forceinline__ int exact_packed(const uint32_t* __restrict__ w32, in
             if (k == NB - 1) ok &= last_ok;
             const uint32_t open = ~closed & ok;
             sum = (int)__dp4a(vb & open, vb, (unsigned)sum);
-            open_bits += __popc(open);
+            open255 = (int)__dp4a(open, 0x01010101u, (unsigned)open255);
         }
     }
-    const int flag = open_bits >> 3;
-    constexpr int kPixCount = (2 * B + 1) * (2 * B + 1);
-    if (flag > kPixCount - 3) return rms_window<B>(sum, flag);
-    return -1;
+    // flag = open255 / 255; replaced when flag > P - 3, and then flag is
+    // P - 2, P - 1 or P, whose reciprocals are constants.
+    constexpr int P = (2 * B + 1) * (2 * B + 1);
+    if (open255 <= 255 * (P - 3)) return -1;
+    const unsigned m = open255 == 255 * P ? recip32(P) : (open255 == 255 * (P - 1) ? recip32(P - 1) : recip32(P - 2));
+    return rms_div(sum, m);
 }
 
 // Image columns [gx0, gx0 + 16) of row gy of a dense caller image (rows x

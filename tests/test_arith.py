@@ -198,7 +198,8 @@ def test_swar_window_evaluation_matches_definition():
     """The list passes' whole evaluation of Algorithm 2 from byte words (rows
     of 2 beta + 1 values, four per word; beta 2 gathers the fifth value of
     rows 0-3 into one word): the sum of the open values' squares (4-way dot
-    products) and their count (population counts), against the definition,
+    products) and their count (a second dot product with 0x01010101: 255
+    per open value), against the definition,
     on random windows of beta 1, 2 and 3 with values near the centre."""
     import numpy as np
     rng = np.random.default_rng(11)
@@ -231,14 +232,14 @@ def test_swar_window_evaluation_matches_definition():
             words = np.array(words, dtype=np.uint64)
             lo = np.full(words.shape, max(ip - alpha + 1, 0)); hi = np.full(words.shape, min(ip + alpha, 255))
             closed = _bytes_in_range(words, lo, hi)
-            s, nopen = 0, 0
+            s, open255 = 0, 0
             for word, c, ok in zip(words.tolist(), closed.tolist(), oks):
                 open_ = ~c & ok & 0xFFFFFFFF
                 for j in range(4):
-                    if (open_ >> (8 * j)) & 0xFF:
-                        b = (word >> (8 * j)) & 0xFF
-                        s += b * b
-                nopen += bin(open_).count("1")
+                    ob = (open_ >> (8 * j)) & 0xFF
+                    b = (word >> (8 * j)) & 0xFF
+                    s += (b & ob) * b     # dp4a(v & open, v)
+                    open255 += ob * 1     # dp4a(open, 0x01010101)
             op = ~((win > ip - alpha) & (win <= ip + alpha))
-            assert nopen // 8 == int(op.sum()) and nopen % 8 == 0, (beta, trial)
+            assert open255 == 255 * int(op.sum()), (beta, trial)
             assert s == int((win.astype(np.int64) ** 2 * op).sum()), (beta, trial)
