@@ -306,21 +306,25 @@ __device__ __forceinline__ void staged_append(StagedList& sl, uint32_t* list, un
 
 // Block-collective (all threads): write every warp's staged entries to the
 // global list with one atomic per CTA.  `counts` is shared scratch of one int
-// per warp plus one.
+// per warp plus one; at most 32 warps.
 __device__ __forceinline__ void staged_flush(StagedList& sl, uint32_t* list, unsigned* n, unsigned cap,
                                              int* counts, int nwarps) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     __syncwarp();
     if (lane == 0) counts[warp] = sl.n;
     __syncthreads();
-    if (tid == 0) {
-        int total = 0;
-        for (int w = 0; w < nwarps; ++w) {
-            const int c = counts[w];
-            counts[w] = total;
-            total += c;
+    if (warp == 0) {
+        // Exclusive prefix of the warps' counts (nwarps <= 32) by shuffles.
+        const int c = lane < nwarps ? counts[lane] : 0;
+        int incl = c;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, d);
+            if (lane >= d) incl += v;
         }
-        counts[nwarps] = total ? (int)atomicAdd(n, (unsigned)total) : 0;
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (lane < nwarps) counts[lane] = incl - c;
+        if (lane == 0) counts[nwarps] = total ? (int)atomicAdd(n, (unsigned)total) : 0;
     }
     __syncthreads();
     const unsigned base = (unsigned)counts[nwarps] + (unsigned)counts[warp];

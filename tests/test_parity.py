@@ -250,6 +250,26 @@ def test_tall_and_wide_extremes(oracle_mod, den, torch_cuda):
         assert_same(oracle_mod, den, torch_cuda, noisy, 10, 1, 8)
 
 
+@pytest.mark.parametrize("beta", [1, 2])
+def test_tall_tiles_on_a_ragged_large_image(torch_cuda, beta):
+    """Single images of at least 32 Mi pixels run the 128-row fused tiles;
+    a 5803 x 5795 image (33.6 M pixels, neither side a multiple of the
+    tile) at 40 % impulses against the oracle run band by band on all host
+    cores: every byte, k and the converged flag."""
+    import oracle_pool
+    from paper_1306_5390_gb300 import build, hgrms
+    build.build()
+    rows, cols, max_k = 5803, 5795, 16
+    _, noisy = synth.noisy_image(rows, cols, 0.40, synth.seed_for(30, beta))
+    ref, k_ref, c_ref, _ = oracle_pool.banded_denoise(noisy, 10, beta, max_k)
+    with hgrms.Denoiser(0) as d:
+        t = torch_cuda.from_numpy(noisy).cuda()
+        k = d.denoise(t, 10, beta, max_k)
+        assert d.stats()["tile_rows"] == 128 - 2 * (hgrms.hgrms_default_passes(beta) - 1) * beta
+        out = t.cpu().numpy()
+        assert k == k_ref and d.converged() == c_ref and int((out != ref).sum()) == 0
+
+
 def test_argument_errors_leave_image_untouched(den, torch_cuda):
     from paper_1306_5390_gb300 import hgrms
     torch = torch_cuda
