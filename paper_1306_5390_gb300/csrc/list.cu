@@ -7,8 +7,9 @@
 // pass changed and evaluates every pixel q within beta of one of them once,
 // by the changed pixel p that "owns" q: the first changed pixel, in raster
 // order, of q's window (read from the previous pass's change bitmap).  For
-// beta 1 one thread takes one (changed pixel, window offset) pair and
-// evaluates q if p owns it.  For wider windows one thread takes one (changed
+// beta 1 one thread takes one changed pixel p, loads its 5 x 5
+// neighbourhood and evaluates the pixels of p's 3 x 3 window that p owns
+// from registers.  For wider windows one thread takes one (changed
 // pixel, window row) pair, decides ownership for the whole row from one
 // bitmap word per window row, and queues the owned pixels in shared memory;
 // the CTA then evaluates its queue with all threads, so the evaluations run
@@ -50,6 +51,18 @@ __device__ __forceinline__ uint32_t row_bits(const uint32_t* __restrict__ row, i
     const uint32_t a = (w0 >= 0 && w0 < nwords) ? __ldca(row + w0) : 0u;
     const uint32_t b = (w0 + 1 >= 0 && w0 + 1 < nwords) ? __ldca(row + w0 + 1) : 0u;
     return sh ? ((a >> sh) | (b << (32 - sh))) : a;
+}
+
+// Warp-wide exclusive prefix sum of n; *total receives the sum.
+__device__ __forceinline__ int warp_excl_scan_l(const int lane, const int n, int* total) {
+    int incl = n;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+    }
+    *total = __shfl_sync(0xffffffffu, incl, 31);
+    return incl - n;
 }
 
 // Algorithm 2 for an interior pixel (card <= 2 is implied by flag >
@@ -306,8 +319,8 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
         // before the bitmap clearing below so that the two loads overlap.
         uint32_t pk_first = 0u;
         if (n <= a.list_cap) {
-            const long long i0 = B == 1 ? warp_base + lane : (long long)tid * gridDim.x + blockIdx.x;
-            const long long per = B == 1 ? P : W;
+            const long long i0 = (long long)tid * gridDim.x + blockIdx.x;
+            const long long per = B == 1 ? 1 : W;
             if (i0 < (long long)n * per) pk_first = __ldcg(prev + (unsigned)(i0 / per));
         }
         // Clear bitmap sc (written by pass t - 2, read by pass t - 1) for pass
@@ -328,66 +341,108 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
             }
         }
         if (n <= a.list_cap && B == 1) {
-            // beta 1 (nine window offsets): one thread per (changed pixel p,
-            // window offset) pair, which measured faster there than the
-            // two-phase form below.
-            const long long total = (long long)n * P;
-            // The list entry of the next iteration is loaded one iteration early.
-            long long i = warp_base + lane;
+            // beta 1: one thread per changed pixel p.  It loads p's 5 x 5
+            // neighbourhood and the previous pass's change bits of the rows
+            // up to p's, and evaluates every pixel q of p's 3 x 3 window
+            // that p owns (no changed pixel of q's window precedes p in
+            // raster order) from those registers.  Changed pixels are dealt
+            // to the CTAs in turn.
+            long long i = (long long)tid * gridDim.x + blockIdx.x;
             uint32_t pk = pk_first;
-            for (long long base = warp_base; base < total; base += gthreads, i += gthreads) {
+            for (long long c0 = 0; c0 + blockIdx.x < (long long)n; c0 += gthreads, i += gthreads) {
                 const long long inext = i + gthreads;
-                const uint32_t pk_next = inext < total ? __ldcg(prev + (unsigned)(inext / P)) : 0u;
-                bool ch = false;
-                uint32_t v = 0;
+                const uint32_t pk_next = inext < (long long)n ? __ldcg(prev + (unsigned)inext) : 0u;
+                uint32_t chm = 0u;  // bit (dy + 1) * 3 + dx + 1: q = p + (dy, dx) changed
                 unsigned img = 0;
-                if (i < total) {
-                    const int o = (int)(i % P);
-                    const int dy = o / W - B, dx = o - (o / W) * W - B;
-                    int py, px;
+                int py = 0, px = 0;
+                if (i < (long long)n) {
                     unpack_entry(pk, xb, yb, img, py, px);
                     const ImgDesc d = kBatch ? load_desc(a.imgs, img) : one;
-                    const int y = py + dy, x = px + dx;
-                    if (y >= B && y < d.rows - B && x >= B && x < d.cols - B) {
-                        const uint32_t* bmp = bm_prev + d.bm_off;
-                        const uint8_t* in = in_arena + d.off + (long long)kPadY * d.pitch + kPadX;
-                        // Issue every load first: the bitmap rows of q's
-                        // window up to p's row, and q's window itself.
-                        uint32_t rb[2 * B + 1];
+                    const uint32_t* bmp = bm_prev + d.bm_off;
+                    const uint8_t* in = in_arena + d.off + (long long)kPadY * d.pitch + kPadX;
+                    uint8_t* out = out_arena + d.off + (long long)kPadY * d.pitch + kPadX;
+                    // Change bits of rows py - 2 .. py, columns px - 2 .. (bit j: column px - 2 + j).
+                    uint32_t rb[3];
 #pragma unroll
-                        for (int r = 0; r <= 2 * B; ++r) {
-                            const int gy = y - B + r;
-                            rb[r] = (gy <= py) ? row_bits(bmp + (size_t)gy * d.bm_words, d.bm_words, x - B) : 0u;
-                        }
-                        constexpr int NW = (W + 3) / 4;
-                        uint32_t win[W][NW];
-                        const long long off = (long long)y * d.pitch + x;
+                    for (int r = 0; r < 3; ++r) {
+                        const int gy = py - 2 + r;
+                        rb[r] = gy >= 0 ? row_bits(bmp + (size_t)gy * d.bm_words, d.bm_words, px - 2) : 0u;
+                    }
+                    // Rows py - 2 .. py + 2, bytes px - 2 .. px + 2 (the canvas padding keeps them in bounds).
+                    uint32_t nb[5][2];
+                    const long long off = (long long)py * d.pitch + px;
 #pragma unroll
-                        for (int r = 0; r < W; ++r) load_row_bytes<W>(in + off + (long long)(r - B) * d.pitch - B, win[r]);
-                        // Ownership: no changed pixel of q's window precedes p
-                        // in raster order (rows above p's, then p's row left of p).
-                        bool owner = true;
+                    for (int r = 0; r < 5; ++r) load_row_bytes<5>(in + off + (long long)(r - 2) * d.pitch - 2, nb[r]);
 #pragma unroll
-                        for (int r = 0; r <= 2 * B; ++r) {
-                            const int gy = y - B + r;
-                            if (gy < py && (rb[r] & ((1u << W) - 1u))) owner = false;
-                            if (gy == py && B - dx > 0 && (rb[r] & ((1u << (B - dx)) - 1u))) owner = false;
-                        }
-                        if (owner) {
+                    for (int dy = -1; dy <= 1; ++dy)
+#pragma unroll
+                        for (int dx = -1; dx <= 1; ++dx) {
+                            const int qy = py + dy, qx = px + dx;
+                            if (qy < 1 || qy >= d.rows - 1 || qx < 1 || qx >= d.cols - 1) continue;
+                            // Ownership: q's window rows above p's hold no change, and
+                            // p's row none left of p (bits dx + 1 .. 1).
+                            bool owner = true;
+#pragma unroll
+                            for (int r = dy + 1; r <= dy + 3; ++r) {
+                                if (r < 2 && (rb[r] & (7u << (dx + 1)))) owner = false;
+                                if (r == 2 && (rb[2] & 3u & ~((1u << (dx + 1)) - 1u))) owner = false;
+                            }
+                            if (!owner) continue;
+                            uint32_t w3[3][1];
+#pragma unroll
+                            for (int r = 0; r < 3; ++r)
+                                w3[r][0] = __funnelshift_r(nb[dy + 1 + r][0], nb[dy + 1 + r][1], 8 * (dx + 1));
+                            const int ip = (int)((w3[1][0] >> 8) & 0xffu);
+                            const int nv = eval_window<1>(w3, a.alpha);
                             ++evals;
-                            const int ip = (int)((win[B][B / 4] >> (8 * (B % 4))) & 0xffu);
-                            const int nv = eval_window<B>(win, a.alpha);
-                            out_arena[d.off + (long long)kPadY * d.pitch + kPadX + off] = (uint8_t)nv;
+                            out[(long long)qy * d.pitch + qx] = (uint8_t)nv;
                             if (nv != ip) {
-                                ch = true;
-                                v = pack_entry(img, y, x, xb, yb);
-                                atomicOr(bm_next + d.bm_off + (size_t)y * d.bm_words + (x >> 5), 1u << (x & 31));
+                                chm |= 1u << ((dy + 1) * 3 + dx + 1);
+                                atomicOr(bm_next + d.bm_off + (size_t)qy * d.bm_words + (qx >> 5), 1u << (qx & 31));
                             }
                         }
+                }
+                if (kBatch && a.img_k) mark_image(s_imgbits, chm != 0u, img, lane);
+                // Append the changed pixels (one warp scan per round).
+                {
+                    int total;
+                    const int cnt = __popc(chm);
+                    const int off = warp_excl_scan_l(lane, cnt, &total);
+                    if (total) {
+                        if (sl.n + total > StagedList::kCap) {
+                            __syncwarp();
+                            unsigned base = 0;
+                            if (lane == 0) base = atomicAdd(nnext, (unsigned)sl.n);
+                            base = __shfl_sync(0xffffffffu, base, 0);
+                            for (int e = lane; e < sl.n; e += 32)
+                                if (base + e < a.list_cap) next[base + e] = sl.buf[e];
+                            __syncwarp();
+                            sl.n = 0;
+                        }
+                        if (total > StagedList::kCap) {
+                            // More than a staging buffer holds: straight to the list.
+                            unsigned base = 0;
+                            if (lane == 0) base = atomicAdd(nnext, (unsigned)total);
+                            unsigned pos = __shfl_sync(0xffffffffu, base, 0) + (unsigned)off;
+                            while (chm) {
+                                const int bt = __ffs(chm) - 1;
+                                chm &= chm - 1u;
+                                if (pos < a.list_cap) next[pos] = pack_entry(img, py + bt / 3 - 1, px + bt % 3 - 1, xb, yb);
+                                ++pos;
+                            }
+                        } else {
+                            int pos = sl.n + off;
+                            while (chm) {
+                                const int bt = __ffs(chm) - 1;
+                                chm &= chm - 1u;
+                                sl.buf[pos++] = pack_entry(img, py + bt / 3 - 1, px + bt % 3 - 1, xb, yb);
+                            }
+                            sl.n += total;
+                        }
+                        __syncwarp();
+                        sl.total += (unsigned)total;
                     }
                 }
-                if (kBatch && a.img_k) mark_image(s_imgbits, ch, img, lane);
-                staged_append(sl, next, nnext, a.list_cap, ch, v, lane);
                 pk = pk_next;
             }
         } else if (n <= a.list_cap) {

@@ -67,3 +67,46 @@ def test_every_candidate_pixel_has_one_owner(beta):
                 interior = beta <= y < rows - beta and beta <= x < cols - beta
                 near = bm[max(0, y - beta):y + beta + 1, max(0, x - beta):x + beta + 1].any()
                 assert count[y, x] == (1 if interior and near else 0), (beta, trial, y, x)
+
+
+def owned_beta1(bm, py, px):
+    """beta 1, one task per changed pixel p: the (dy, dx) of p's 3 x 3 window
+    that p owns, with the kernel's masks.  rb[r] = the changes of row
+    py - 2 + r (r = 0, 1, 2: the rows up to p's), columns px - 2 .. (bit j:
+    column px - 2 + j); q = p + (dy, dx) has window rows r = dy + 1 .. dy + 3
+    and window columns bits dx + 1 .. dx + 3: rows above p's (r < 2) must
+    hold none of them, p's row (r = 2) none left of p (bits dx + 1 .. 1)."""
+    rows, cols = bm.shape
+    rb = [row_bits(bm, py - 2 + r, px - 2, 32) if py - 2 + r >= 0 else 0 for r in range(3)]
+    out = set()
+    for dy in (-1, 0, 1):
+        for dx in (-1, 0, 1):
+            qy, qx = py + dy, px + dx
+            if not (1 <= qy < rows - 1 and 1 <= qx < cols - 1):
+                continue
+            owner = True
+            for r in range(dy + 1, dy + 4):
+                if r < 2 and rb[r] & (7 << (dx + 1)):
+                    owner = False
+                if r == 2 and rb[2] & 3 & ~((1 << (dx + 1)) - 1):
+                    owner = False
+            if owner:
+                out.add((dy, dx))
+    return out
+
+
+def test_beta1_per_changed_pixel_tasks_one_owner():
+    rng = np.random.default_rng(2013)
+    for trial in range(60):
+        rows = int(rng.integers(3, 30))
+        cols = int(rng.integers(3, 30))
+        bm = rng.random((rows, cols)) < rng.choice([0.02, 0.1, 0.3, 0.7, 1.0])
+        count = np.zeros((rows, cols), dtype=int)
+        for py, px in zip(*np.nonzero(bm)):
+            for dy, dx in owned_beta1(bm, int(py), int(px)):
+                count[py + dy, px + dx] += 1
+        for y in range(rows):
+            for x in range(cols):
+                interior = 1 <= y < rows - 1 and 1 <= x < cols - 1
+                near = bm[max(0, y - 1):y + 2, max(0, x - 1):x + 2].any()
+                assert count[y, x] == (1 if interior and near else 0), (trial, y, x)
