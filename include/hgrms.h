@@ -334,7 +334,8 @@ int hgrms_predictor_grad(hgrms_t h, const float* weights, const float* x0, const
 #define HGRMS_OPT_TILE_EVAL_MAX 7 /* fused kernel: a pass runs as an in-tile list pass while the previous
                                      pass's changes need at most this many evaluations in the tile,
                                      else as a dense pass (0 = built-in: 2048 for beta 2, else
-                                     4096) */
+                                     4096, per 64-row tile; twice that with the 128-row tiles of
+                                     calls of at least 32 Mi pixels) */
 
 #define HGRMS_OPT_TMA      13 /* 1 = the default schedule's fused launches (beta <= 4) stage each tile
                                    with its halo in shared memory by TMA, the next tile's load running

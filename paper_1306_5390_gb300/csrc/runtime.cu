@@ -35,7 +35,8 @@
 
 #define HG_EXPORT extern "C" __attribute__((visibility("default")))
 
-// Fused passes per launch and in-tile list/dense switch point of one call.
+// Fused passes per launch and in-tile list/dense switch point of one call
+// (0: the built-in one for the call's tiles).
 struct Tuning {
     int T;
     int eval_max;
@@ -162,9 +163,10 @@ namespace {
 // for wider windows, whose fused passes cost more than list passes even on
 // dense change sets.  With HGRMS_OPT_RELAUNCH_PPM set, up to 8 for any beta.
 constexpr int kDefaultRelaunches = 3;
-// Single images of at least this many pixels use the 128-row tiles (where
-// compiled): measured faster on 8192 x 8192; smaller images keep the 64-row
-// tiles, whose larger tile count spreads better over the SMs.
+// Calls of at least this many pixels use the 128-row tiles (where compiled
+// and they compute fewer rows): measured faster on 8192 x 8192 and on the
+// 629 M-pixel uneven batch; smaller calls keep the 64-row tiles, whose larger
+// tile count spreads better over the SMs.
 constexpr long long kTallMinPixels = 32ll << 20;
 constexpr long long kRelaunchMinPixels = 4ll << 20;
 constexpr size_t kMaxGraphs = 8;  // captured graphs kept per handle (HGRMS_OPT_GRAPH)
@@ -608,14 +610,24 @@ int finish_hybrid(hgrms_ctx* h, const hgrms_ctx::PendingCall& pd, const BatchImg
 int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int max_k, int* k_out,
                const Tuning& tu, bool write_back, float* ms, int forced_fused = 0, bool async_call = false) {
     const int T = tu.T;
-    // One large image takes the tall tiles when they are compiled for its
-    // (beta, T): at this size every SM still gets many tiles.
-    long long px_call = 0;
-    for (int i = 0; i < n; ++i) px_call += (long long)im[i].rows * im[i].cols;
-    const hg::FusedEntry* fe = nullptr;
-    if (n == 1 && px_call >= kTallMinPixels) fe = find_fused(beta, T, 128);
-    if (!fe) fe = find_fused(beta, T);
+    // Large calls (one image or a batch) take the tall tiles when they are
+    // compiled for (beta, T) and compute fewer rows with them: at this size
+    // every SM still gets many tiles.
+    const hg::FusedEntry* fe = find_fused(beta, T);
     if (!fe) return HGRMS_EINVAL;
+    {
+        const hg::FusedEntry* tall = find_fused(beta, T, 128);
+        long long px_call = 0, rows64 = 0, rows128 = 0;
+        for (int i = 0; i < n && tall; ++i) {
+            const long long tx = (im[i].cols + fe->TW - 1) / fe->TW;
+            px_call += (long long)im[i].rows * im[i].cols;
+            rows64 += tx * ((im[i].rows + fe->TH - 1) / fe->TH) * 64;
+            rows128 += tx * ((im[i].rows + tall->TH - 1) / tall->TH) * 128;
+        }
+        if (tall && px_call >= kTallMinPixels && rows128 < rows64) fe = tall;
+    }
+    // The built-in in-tile switch point counts evaluations per 64-row tile.
+    const int eval_max = tu.eval_max > 0 ? tu.eval_max : default_eval_max(beta) * (fe->RN / 64);
     const bool per_image_k = n > 1;
     // Layout: image i's canvas at offset off_i of each arena, its bitmap at
     // word bm_off_i of each bitmap arena, its tiles from tile0_i.
@@ -699,7 +711,7 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
     a.img_k = per_image_k ? h->img_k : nullptr;
     a.ntiles = (int)tiles_total;
     a.hybrid = 1;
-    a.tile_eval_max = tu.eval_max;
+    a.tile_eval_max = eval_max;
     a.user0 = (n == 1 && im[0].dev) ? im[0].ptr : nullptr;
     {
         int user_ok = 0;
@@ -854,7 +866,7 @@ int run_hybrid(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int
     pd.launches = launches;
     pd.fused_launches = fused_launches;
     pd.T = T;
-    pd.eval_max = tu.eval_max;
+    pd.eval_max = eval_max;
     pd.TH = fe->TH;
     pd.TW = fe->TW;
     pd.tiles_total = tiles_total;
@@ -933,8 +945,7 @@ int finish_hybrid(hgrms_ctx* h, const hgrms_ctx::PendingCall& pd, const BatchImg
 // values.
 int choose_tuning(hgrms_ctx* h, const BatchImg* im, int n, int alpha, int beta, int max_k, int* k_scratch,
                   Tuning* out) {
-    Tuning tu{h->opt_passes > 0 ? h->opt_passes : default_passes(beta),
-              h->opt_tile_eval_max > 0 ? h->opt_tile_eval_max : default_eval_max(beta)};
+    Tuning tu{h->opt_passes > 0 ? h->opt_passes : default_passes(beta), h->opt_tile_eval_max};
     if (!h->opt_autotune || (h->opt_passes > 0 && h->opt_tile_eval_max > 0)) {
         *out = tu;
         return HGRMS_OK;
