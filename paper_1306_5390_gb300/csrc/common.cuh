@@ -231,6 +231,18 @@ __device__ __forceinline__ uint32_t prmt_sign(uint32_t a, uint32_t b, uint32_t s
     return d;
 }
 
+// Warp-wide exclusive prefix sum of n; *total receives the sum.
+__device__ __forceinline__ int warp_excl_scan(const int lane, const int n, int* total) {
+    int incl = n;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const int v = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += v;
+    }
+    *total = __shfl_sync(0xffffffffu, incl, 31);
+    return incl - n;
+}
+
 // Passes the launch must run: 0 when the call has finished.
 __device__ __forceinline__ int launch_passes(const Ctrl* c, int T) {
     unsigned k = __ldcg(&c->k);
@@ -304,6 +316,49 @@ __device__ __forceinline__ void staged_append(StagedList& sl, uint32_t* list, un
     sl.total += (unsigned)__popc(bal);
 }
 
+// Warp-collective: append entry(b) for every set bit b of this lane's mask m
+// (one warp scan for the whole warp).  A round that does not fit the buffer
+// writes it out first; one larger than a whole buffer goes straight to the
+// list.
+template <class Entry>
+__device__ __forceinline__ void staged_append_mask(StagedList& sl, uint32_t* list, unsigned* n, unsigned cap,
+                                                   uint32_t m, int lane, Entry entry) {
+    int total;
+    const int off = warp_excl_scan(lane, __popc(m), &total);
+    if (!total) return;
+    if (sl.n + total > StagedList::kCap) {
+        __syncwarp();
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(n, (unsigned)sl.n);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        for (int e = lane; e < sl.n; e += 32)
+            if (base + e < cap) list[base + e] = sl.buf[e];
+        __syncwarp();
+        sl.n = 0;
+    }
+    if (total > StagedList::kCap) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(n, (unsigned)total);
+        unsigned pos = __shfl_sync(0xffffffffu, base, 0) + (unsigned)off;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1u;
+            if (pos < cap) list[pos] = entry(b);
+            ++pos;
+        }
+    } else {
+        int pos = sl.n + off;
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1u;
+            sl.buf[pos++] = entry(b);
+        }
+        sl.n += total;
+    }
+    __syncwarp();
+    sl.total += (unsigned)total;
+}
+
 // Block-collective (all threads): write every warp's staged entries to the
 // global list with one atomic per CTA.  `counts` is shared scratch of one int
 // per warp plus one; at most 32 warps.
@@ -314,16 +369,10 @@ __device__ __forceinline__ void staged_flush(StagedList& sl, uint32_t* list, uns
     if (lane == 0) counts[warp] = sl.n;
     __syncthreads();
     if (warp == 0) {
-        // Exclusive prefix of the warps' counts (nwarps <= 32) by shuffles.
-        const int c = lane < nwarps ? counts[lane] : 0;
-        int incl = c;
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int v = __shfl_up_sync(0xffffffffu, incl, d);
-            if (lane >= d) incl += v;
-        }
-        const int total = __shfl_sync(0xffffffffu, incl, 31);
-        if (lane < nwarps) counts[lane] = incl - c;
+        // Exclusive prefix of the warps' counts (nwarps <= 32).
+        int total;
+        const int ex = warp_excl_scan(lane, lane < nwarps ? counts[lane] : 0, &total);
+        if (lane < nwarps) counts[lane] = ex;
         if (lane == 0) counts[nwarps] = total ? (int)atomicAdd(n, (unsigned)total) : 0;
     }
     __syncthreads();

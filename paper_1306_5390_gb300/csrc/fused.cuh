@@ -443,18 +443,6 @@ __device__ __forceinline__ void flush_candidates(PassCtx<B, T, RN>& c, const int
     c.ncand = 0;
 }
 
-// Warp-wide exclusive prefix sum of n; *total receives the sum.
-__device__ __forceinline__ int warp_excl_scan(const int lane, const int n, int* total) {
-    int incl = n;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += v;
-    }
-    *total = __shfl_sync(0xffffffffu, incl, 31);
-    return incl - n;
-}
-
 // Append candidate bits (bit 8r + i: row ys + r, pixel x + i) to the warp list.
 template <int B, int T, int RN>
 __device__ __forceinline__ void append_bits(PassCtx<B, T, RN>& c, const int lane, uint32_t m, const int ys,

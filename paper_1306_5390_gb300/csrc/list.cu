@@ -53,18 +53,6 @@ __device__ __forceinline__ uint32_t row_bits(const uint32_t* __restrict__ row, i
     return sh ? ((a >> sh) | (b << (32 - sh))) : a;
 }
 
-// Warp-wide exclusive prefix sum of n; *total receives the sum.
-__device__ __forceinline__ int warp_excl_scan_l(const int lane, const int n, int* total) {
-    int incl = n;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        const int v = __shfl_up_sync(0xffffffffu, incl, d);
-        if (lane >= d) incl += v;
-    }
-    *total = __shfl_sync(0xffffffffu, incl, 31);
-    return incl - n;
-}
-
 // Algorithm 2 for an interior pixel (card <= 2 is implied by flag >
 // pix_count - 3 for alpha >= 1, and card is 0 for alpha = 0).  `p` points at
 // the pixel in a row-major byte array with row stride `stride`.
@@ -404,45 +392,9 @@ __global__ void __launch_bounds__(kListThreads, 2) list_loop_kernel(PassArgs a) 
                 }
                 if (kBatch && a.img_k) mark_image(s_imgbits, chm != 0u, img, lane);
                 // Append the changed pixels (one warp scan per round).
-                {
-                    int total;
-                    const int cnt = __popc(chm);
-                    const int off = warp_excl_scan_l(lane, cnt, &total);
-                    if (total) {
-                        if (sl.n + total > StagedList::kCap) {
-                            __syncwarp();
-                            unsigned base = 0;
-                            if (lane == 0) base = atomicAdd(nnext, (unsigned)sl.n);
-                            base = __shfl_sync(0xffffffffu, base, 0);
-                            for (int e = lane; e < sl.n; e += 32)
-                                if (base + e < a.list_cap) next[base + e] = sl.buf[e];
-                            __syncwarp();
-                            sl.n = 0;
-                        }
-                        if (total > StagedList::kCap) {
-                            // More than a staging buffer holds: straight to the list.
-                            unsigned base = 0;
-                            if (lane == 0) base = atomicAdd(nnext, (unsigned)total);
-                            unsigned pos = __shfl_sync(0xffffffffu, base, 0) + (unsigned)off;
-                            while (chm) {
-                                const int bt = __ffs(chm) - 1;
-                                chm &= chm - 1u;
-                                if (pos < a.list_cap) next[pos] = pack_entry(img, py + bt / 3 - 1, px + bt % 3 - 1, xb, yb);
-                                ++pos;
-                            }
-                        } else {
-                            int pos = sl.n + off;
-                            while (chm) {
-                                const int bt = __ffs(chm) - 1;
-                                chm &= chm - 1u;
-                                sl.buf[pos++] = pack_entry(img, py + bt / 3 - 1, px + bt % 3 - 1, xb, yb);
-                            }
-                            sl.n += total;
-                        }
-                        __syncwarp();
-                        sl.total += (unsigned)total;
-                    }
-                }
+                staged_append_mask(sl, next, nnext, a.list_cap, chm, lane, [&](int bt) {
+                    return pack_entry(img, py + bt / 3 - 1, px + bt % 3 - 1, xb, yb);
+                });
                 pk = pk_next;
             }
         } else if (n <= a.list_cap) {
