@@ -94,10 +94,10 @@ struct FusedGeo {
     // appends every 4 rows (measured faster than 2), the others every 2, which
     // keeps the lists small enough for the TMA staging buffer.
     static constexpr int kAppendRows = B == 2 ? 4 : 2;
-    // beta 3: dense passes count in two stages (band_dense2; for beta 2 the
+    // beta 3: dense passes count in stages (band_dense2; for beta 2 the
     // single-stage count measured faster); the second half of a warp's
-    // candidate buffer then holds its stage-two work list (at most 4 pixel
-    // pairs per lane and row of a kAppendRows-row group).
+    // candidate buffer then holds its work list of unsettled pixel pairs (at
+    // most 4 per lane and row of a kAppendRows-row group).
     static constexpr bool kTwoStage = B == 3 && kRows == 8;
     static constexpr int kCandCap = kAppendRows * 256;  // per-warp candidate list
     static constexpr int kCandLimit = kTwoStage ? kCandCap / 2 : kCandCap;
@@ -661,26 +661,25 @@ __device__ __forceinline__ void band_dense_sym(PassCtx<B, T, RN>& c, const int y
         append_bits<B, T, RN>(c, lane, (uint32_t)((m64 >> (8 * kA * g)) & kAMask), ys + kA * g, 2 * ws);
 }
 
-// Outer-ring closed-neighbour count of one pixel pair (the fp16 pair at
-// word xw of tile row y): the window positions with |dy| >= 2 or |dx| >= 2,
-// summed as integers (see the header; 40 results for beta 3).
-template <int B, int SWW>
-__device__ __forceinline__ uint32_t outer_count(const uint32_t* __restrict__ in, const int y, const int xw,
-                                                const __half2 cp, const __half2 two_a) {
-    constexpr int WB = (B + 1) / 2;  // words needed beyond each side of the pair
+// Closed-neighbour count of one pixel pair (the fp16 pair at word xw of
+// tile row y) over the window positions at Chebyshev distance exactly D,
+// summed as integers (see the header): 16 results for D = 2, 24 for D = 3.
+template <int D, int SWW>
+__device__ __forceinline__ uint32_t ring_count(const uint32_t* __restrict__ in, const int y, const int xw,
+                                               const __half2 cp, const __half2 two_a) {
+    constexpr int WB = (D + 1) / 2;
     const __half2 m2 = __float2half2_rn(-2.f);
     uint32_t acc = 0u, pend = 0u;
     int n = 0;
 #pragma unroll
-    for (int dy = -B; dy <= B; ++dy) {
+    for (int dy = -D; dy <= D; ++dy) {
         const uint32_t* row = in + (y + dy) * SWW + xw;
         uint32_t w[2 * WB + 1];
 #pragma unroll
         for (int k = 0; k <= 2 * WB; ++k) w[k] = row[k - WB];
 #pragma unroll
-        for (int dx = -B; dx <= B; ++dx) {
-            if (dy >= -1 && dy <= 1 && dx >= -1 && dx <= 1) continue;
-            // fp16 pair of the pixels at offsets dx, dx + 1 from the pair's first pixel
+        for (int dx = -D; dx <= D; ++dx) {
+            if (dy > -D && dy < D && dx > -D && dx < D) continue;
             const uint32_t pw = (dx & 1) ? __byte_perm(w[WB + (dx - 1) / 2], w[WB + (dx + 1) / 2], 0x5432)
                                          : w[WB + dx / 2];
             const __half2 e = __hsub2(u2h(pw), cp);
@@ -692,17 +691,19 @@ __device__ __forceinline__ uint32_t outer_count(const uint32_t* __restrict__ in,
             ++n;
         }
     }
+    if (n & 1) acc += pend;
     return acc;
 }
 
-// Dense pass over the warp's 8-row band in two stages (beta 3), in groups of
+// Dense pass over the warp's 8-row band in stages (beta 3), in groups of
 // kAppendRows rows.  Stage one counts every pixel's closed neighbours in the
 // inner 3 x 3 ring, packed as in band_dense; a pixel with two or more already
 // has too many to be a candidate.  The other pixels' pairs go to a per-warp
-// work list (row, lane, pair and the pixels' stage-one state: not settled,
-// one closed neighbour) and stage two counts only the outer ring for them,
-// one pair per lane.  Pixels with at most one closed neighbour in all are
-// candidates.
+// work list (row, lane, pair and the pixels' state: not settled, one closed
+// neighbour so far); stage two counts the ring at distance 2 for them, one
+// pair per lane, and keeps (compacted in place) only the pairs with a pixel
+// still not settled; stage three counts the ring at distance 3 for those.
+// Pixels with at most one closed neighbour in all are candidates.
 template <int B, int T, int RN>
 __device__ __forceinline__ void band_dense2(PassCtx<B, T, RN>& c, const int ys, const int ws, const int lane,
                                             const __half2 two_a) {
@@ -760,20 +761,49 @@ __device__ __forceinline__ void band_dense2(PassCtx<B, T, RN>& c, const int ys, 
             items[pos++] = (uint16_t)((h * kHalf + rr) | (lane << 3) | (j << 8) | (fl << 10));
         }
         __syncwarp();
-        // Stage two.
+        // Stage two (beta 3): the ring at distance 2 for every item; an item
+        // whose pixels are all settled by then leaves the list, the others
+        // are compacted (in place) and stage three counts their ring at
+        // distance 3.  fl: bits 0-1 the pair's unsettled pixels, bits 2-3
+        // those with one closed neighbour so far.
+        int total2 = 0;
         for (int base = 0; base < total; base += 32) {
+            const int i = base + lane;
+            uint32_t e = 0u, keep = 0u;
+            if (i < total) {
+                e = items[i];
+                const int y = ys + (int)(e & 7u);
+                const int xw = ws - 4 * lane + 4 * (int)((e >> 3) & 31u) + (int)((e >> 8) & 3u);
+                const uint32_t fl = e >> 10;
+                const __half2 cpair = __hadd2(u2h(c.in[y * G::SWW + xw]), __float2half2_rn(0.5f));
+                const uint32_t z = ring_count<2, G::SWW>(c.in, y, xw, cpair, two_a) * 47u;
+                const uint32_t blo = (z >> 8) & 0xFFu, bhi = z >> 24;  // 4 K (+ 0..2), K <= 16
+                uint32_t fl2 = 0u;
+                // Still at most one closed neighbour: stays; K so far = 1 when either count had one.
+                if ((fl & 1u) && blo < (((fl >> 2) & 1u) ? 4u : 8u)) fl2 |= 1u | ((((fl >> 2) & 1u) | (blo >= 4u ? 1u : 0u)) << 2);
+                if ((fl & 2u) && bhi < (((fl >> 3) & 1u) ? 4u : 8u)) fl2 |= 2u | ((((fl >> 3) & 1u) | (bhi >= 4u ? 1u : 0u)) << 3);
+                if (fl2) keep = (e & 0x3FFu) | (fl2 << 10);
+            }
+            __syncwarp();  // every lane has read its item before the compacted ones are written
+            const unsigned bal = __ballot_sync(0xffffffffu, keep != 0u);
+            if (keep) items[total2 + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)keep;
+            total2 += __popc(bal);
+        }
+        __syncwarp();
+        // Stage three.
+        for (int base = 0; base < total2; base += 32) {
             const int i = base + lane;
             uint32_t cb = 0u;  // bit h: pixel 2 xw + h is a candidate
             int q0 = 0;
-            if (i < total) {
+            if (i < total2) {
                 const uint32_t e = items[i];
                 const int y = ys + (int)(e & 7u);
                 const int xw = ws - 4 * lane + 4 * (int)((e >> 3) & 31u) + (int)((e >> 8) & 3u);
                 const uint32_t fl = e >> 10;
                 const __half2 cpair = __hadd2(u2h(c.in[y * G::SWW + xw]), __float2half2_rn(0.5f));
-                const uint32_t z = outer_count<B, G::SWW>(c.in, y, xw, cpair, two_a) * 47u;
+                const uint32_t z = ring_count<3, G::SWW>(c.in, y, xw, cpair, two_a) * 47u;
                 const uint32_t blo = (z >> 8) & 0xFFu, bhi = z >> 24;  // 4 K_outer (+ 0..2)
-                // At most one closed neighbour in all: K_outer <= 1 - K_inner.
+                // At most one closed neighbour in all.
                 if ((fl & 1u) && blo < (((fl >> 2) & 1u) ? 4u : 8u)) cb |= 1u;
                 if ((fl & 2u) && bhi < (((fl >> 3) & 1u) ? 4u : 8u)) cb |= 2u;
                 q0 = y * G::SW + 2 * xw;

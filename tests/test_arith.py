@@ -243,3 +243,25 @@ def test_swar_window_evaluation_matches_definition():
             op = ~((win > ip - alpha) & (win <= ip + alpha))
             assert open255 == 255 * int(op.sum()), (beta, trial)
             assert s == int((win.astype(np.int64) ** 2 * op).sum()), (beta, trial)
+
+
+def test_three_stage_decision_table():
+    """beta 3's staged count: after the inner ring (K_in <= 1 for a pixel
+    still in the work list), stage two adds the ring at distance 2 (K_mid <=
+    16) and keeps the pixel when its byte b = 4 K_mid (+ 0..2) is below 4
+    (K_in = 1) or 8 (K_in = 0), recording K_in + K_mid as 1 when K_in = 1 or
+    b >= 4; stage three then applies the two-stage rule with that count.
+    Every combination of the counts, the pair's other pixel only moving the
+    carry: kept exactly when K_in + K_mid <= 1, with the right count."""
+    for k_in in range(2):
+        for k_mid in range(17):
+            for k_other in range(17):
+                for hi in (False, True):
+                    lo_val = (k_other if hi else k_mid) * 0x3C00
+                    hi_val = (k_mid if hi else k_other) * 0x3C00
+                    z = ((lo_val + (hi_val << 16)) % 2**32) * 47 % 2**32
+                    b = (z >> 24) if hi else ((z >> 8) & 0xFF)
+                    kept = b < (4 if k_in == 1 else 8)
+                    assert kept == (k_in + k_mid <= 1), (k_in, k_mid, k_other, hi)
+                    if kept:
+                        assert (1 if (k_in == 1 or b >= 4) else 0) == k_in + k_mid
