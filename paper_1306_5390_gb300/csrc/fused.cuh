@@ -51,8 +51,8 @@
 // of the product is 4 K_lo and byte 3 is 4 K_hi + (0..2): "at most one
 // closed neighbour" is "byte & 0xF8 == 0" for both.
 
-// Work layout: a pass computes rows [R0, R0 + RN) (RN = 128 for beta 1 and
-// 2, else 64) and columns [8, 264).  In a dense pass warp w walks the rows
+// Work layout: a pass computes rows [R0, R0 + RN) (RN = 64, or 128 for the
+// tall instances of beta 1 and 2) and columns [8, 264).  In a dense pass warp w walks the rows
 // [R0 + rw, R0 + rw + r) of its band (r = 4 for beta 1, else 8) with a register ring
 // of the 2 beta + 1 window rows, lane l owning the 8 pixels at columns
 // [8 + 8l, 16 + 8l); candidate pixels (at most one closed neighbour) are
@@ -98,9 +98,9 @@ struct FusedGeo {
     // single-stage count measured faster); the second half of a warp's
     // candidate buffer then holds its work list of unsettled pixel pairs (at
     // most 4 per lane and row of a kAppendRows-row group).
-    static constexpr bool kTwoStage = B == 3 && kRows == 8;
+    static constexpr bool kStaged = B == 3 && kRows == 8;
     static constexpr int kCandCap = kAppendRows * 256;  // per-warp candidate list
-    static constexpr int kCandLimit = kTwoStage ? kCandCap / 2 : kCandCap;
+    static constexpr int kCandLimit = kStaged ? kCandCap / 2 : kCandCap;
     // Changed pixels kept per pass: a list pass needs at most eval_max /
     // (2 beta + 1)^2 of them at the built-in switch points (455 for beta 1,
     // 82 for beta 2, 84 for beta 3); a longer list makes the next pass dense.
@@ -1176,7 +1176,7 @@ fused_kernel(PassArgs a) {
             const bool dense = (t == 0 && !from_map) || nprev > G::kListCap || nprev * G::P > eval_max;
             if (dense) {
                 ++dense_passes;
-                if constexpr (G::kTwoStage)
+                if constexpr (G::kStaged)
                     band_dense2<B, T, RN>(c, ys, ws, lane, two_a);
                 else if constexpr (B <= 2)
                     band_dense_sym<B, T, RN>(c, ys, ws, lane);
