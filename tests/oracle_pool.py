@@ -21,6 +21,14 @@ or ``oracle.denoise``.
     owned rows after max_k passes are the whole image's final result in both
     cases, and every band can simply run max_k passes.
 
+``window_denoise`` - one rectangular window of an image too large for the
+    oracle (the same margin argument in both directions): the crop is the
+    window grown by M pixels on every side (clipped to the image: a crop
+    edge that is an image edge is exact as it is), its centre is exact after
+    every pass up to max_k, and the per-pass change counts inside the window
+    are lower bounds of the whole image's (a pass that changed a window
+    pixel changed the image).
+
 ``batch_denoise`` / ``bsds_denoise`` - independent images of a workload, one
     task per image.  The worker regenerates the image from the workload's
     seed (synth), runs ``oracle.denoise`` and returns the result (with the
@@ -123,3 +131,22 @@ def bsds_denoise(n_images: int = 64):
         for key, r in per_image.items():
             out.setdefault(key, []).append(r)
     return out
+
+
+def window_denoise(img: np.ndarray, y0: int, x0: int, h: int, w: int, alpha: int, beta: int, max_k: int):
+    """The oracle's bytes of img[y0:y0+h, x0:x0+w] after max_k passes and the
+    number of that window's pixels each pass t = 1..max_k changed (see the
+    module docstring), from a crop with a margin of max_k * beta + beta."""
+    import oracle
+    rows, cols = img.shape
+    m = max_k * beta + beta
+    cy0, cx0 = max(0, y0 - m), max(0, x0 - m)
+    cy1, cx1 = min(rows, y0 + h + m), min(cols, x0 + w + m)
+    cur = np.ascontiguousarray(img[cy0:cy1, cx0:cx1], dtype=np.uint8)
+    sy, sx = y0 - cy0, x0 - cx0
+    counts = []
+    for _ in range(max_k):
+        nxt, _ = oracle.one_pass(cur, alpha, beta)
+        counts.append(int((nxt[sy:sy + h, sx:sx + w] != cur[sy:sy + h, sx:sx + w]).sum()))
+        cur = nxt
+    return cur[sy:sy + h, sx:sx + w].copy(), counts
