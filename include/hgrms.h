@@ -238,6 +238,15 @@ int hgrms_server_wait(hgrms_server_t s, unsigned long long id, double timeout_s,
 int hgrms_server_stats(hgrms_server_t s, long long* served, long long* batches, long long* queued,
                        long long* max_in_flight);
 
+/* For tests of the failure path (not for production; 0 at creation): the
+ * next n allocations of a slot's buffer for host images fail as a failing
+ * cudaMalloc would, without calling it.  The requests of each such batch
+ * complete with HGRMS_ENOMEM (hgrms_server_wait returns it, and
+ * hgrms_server_stats reports it as the first error); later batches allocate
+ * again and are served normally.  Replaces any count still pending.  Returns
+ * HGRMS_OK, or HGRMS_EINVAL for a NULL server or n < 0. */
+int hgrms_server_fail_allocations(hgrms_server_t s, int n);
+
 /* Serve every queued request, stop the workers and free everything.  NULL is
  * accepted. */
 void hgrms_server_destroy(hgrms_server_t s);

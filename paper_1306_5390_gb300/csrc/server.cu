@@ -81,6 +81,7 @@ struct hgrms_server {
     cudaStream_t coop = nullptr;  // the slots' list-pass launches, one at a time
     long long served = 0, batches = 0, in_flight = 0, max_in_flight = 0;
     int error = 0;
+    int fail_allocs = 0;  // allocations still to fail (hgrms_server_fail_allocations; under mu)
 
     void work(int slot);
 };
@@ -132,8 +133,19 @@ void hgrms_server::work(int slot) {
             if (dbuf) cudaFree(dbuf);
             dbuf = nullptr;
             dbuf_bytes = 0;
-            if (cudaMalloc(&dbuf, host_bytes) != cudaSuccess) {
+            bool fake = false;  // a failure requested by hgrms_server_fail_allocations
+            {
+                std::lock_guard<std::mutex> lock(mu);
+                if (fail_allocs > 0) {
+                    --fail_allocs;
+                    fake = true;
+                }
+            }
+            if (fake) {
+                rc = HGRMS_ENOMEM;
+            } else if (cudaMalloc(&dbuf, host_bytes) != cudaSuccess) {
                 cudaGetLastError();
+                dbuf = nullptr;
                 rc = HGRMS_ENOMEM;
             } else {
                 dbuf_bytes = host_bytes;
@@ -315,6 +327,13 @@ HG_EXPORT int hgrms_server_stats(hgrms_server_t s, long long* served, long long*
     if (queued) *queued = (long long)s->queue.size();
     if (max_in_flight) *max_in_flight = s->max_in_flight;
     return s->error;
+}
+
+HG_EXPORT int hgrms_server_fail_allocations(hgrms_server_t s, int n) {
+    if (!s || n < 0) return HGRMS_EINVAL;
+    std::lock_guard<std::mutex> lock(s->mu);
+    s->fail_allocs = n;
+    return HGRMS_OK;
 }
 
 HG_EXPORT void hgrms_server_destroy(hgrms_server_t s) {

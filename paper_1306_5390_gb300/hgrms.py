@@ -48,7 +48,8 @@ EXPORTED = (
     "hgrms_converged", "hgrms_strerror", "hgrms_last_cuda_error", "hgrms_set_option",
     "hgrms_stats", "hgrms_launch_times", "hgrms_default_passes", "hgrms_has_kernel",
     "hgrms_denoise_noalloc", "hgrms_server_create", "hgrms_server_submit", "hgrms_server_wait",
-    "hgrms_server_stats", "hgrms_server_destroy", "hgrms_predictor_load", "hgrms_predict_k",
+    "hgrms_server_stats", "hgrms_server_fail_allocations", "hgrms_server_destroy", "hgrms_predictor_load",
+    "hgrms_predict_k",
     "hgrms_predictor_train", "hgrms_predictor_grad", "hgrms_rms",
 )
 
@@ -156,6 +157,8 @@ def load_library(path: str | None = None):
         lib.hgrms_server_wait.restype = ctypes.c_int
         lib.hgrms_server_stats.argtypes = [vp, llp, llp, llp, llp]
         lib.hgrms_server_stats.restype = ctypes.c_int
+        lib.hgrms_server_fail_allocations.argtypes = [vp, ctypes.c_int]
+        lib.hgrms_server_fail_allocations.restype = ctypes.c_int
         lib.hgrms_server_destroy.argtypes = [vp]
         lib.hgrms_server_destroy.restype = None
         fp = ctypes.POINTER(ctypes.c_float)
@@ -487,6 +490,13 @@ class Server:
         err = load_library().hgrms_server_stats(self.h, *[ctypes.byref(x) for x in v])
         return dict(served=v[0].value, batches=v[1].value, queued=v[2].value, max_in_flight=v[3].value,
                     error=err)
+
+    def fail_allocations(self, n: int) -> None:
+        """Tests of the failure path: the next n buffer allocations of the
+        slots fail (hgrms_server_fail_allocations)."""
+        rc = load_library().hgrms_server_fail_allocations(self.h, int(n))
+        if rc < 0:
+            raise HgrmsError(rc, "hgrms_server_fail_allocations")
 
     def close(self) -> None:
         if self.h:

@@ -121,6 +121,7 @@ def test_server_without_device(lib):
         lib.hgrms_server_destroy(h)
     lib.hgrms_server_destroy(None)  # accepted
     assert lib.hgrms_server_wait(None, 1, 0.0, None) == hgrms.HGRMS_EINVAL
+    assert lib.hgrms_server_fail_allocations(None, 1) == hgrms.HGRMS_EINVAL
 
 
 def test_header_constants_match_the_binding():

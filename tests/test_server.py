@@ -113,6 +113,36 @@ def test_tiny_budget_serves_large_requests_alone(oracle_mod, torch_cuda):
             srv.wait(rid)
 
 
+def test_injected_allocation_failure_then_recovery(oracle_mod, torch_cuda):
+    """A failure made on the host, with no GPU fault: the slot's buffer
+    allocation for host images is made to fail.  A device image needs no
+    such buffer and is served; the next host request completes with
+    HGRMS_ENOMEM, its output untouched, and the server reports that error;
+    a pending count can be withdrawn; the requests after it are served with
+    the oracle's bytes and k."""
+    from paper_1306_5390_gb300 import hgrms
+    torch = torch_cuda
+    imgs = [synth.noisy_image(300 + 7 * i, 200 + 5 * i, 0.3, 1500 + i)[1] for i in range(3)]
+    refs = [oracle_mod.denoise(img, 10, 1, 32) for img in imgs]
+    with hgrms.Server(0, hbm_budget_bytes=1 << 30, slots=1) as srv:
+        srv.fail_allocations(1)
+        dev = torch.from_numpy(imgs[0].copy()).cuda()
+        k, _ = srv.wait(srv.submit(dev, 10, 1, 32))
+        assert k == refs[0][1] and np.array_equal(dev.cpu().numpy(), refs[0][0])
+        out = np.zeros_like(imgs[1])
+        with pytest.raises(hgrms.HgrmsError) as err:
+            srv.wait(srv.submit(imgs[1], 10, 1, 32, out=out))
+        assert err.value.code == hgrms.HGRMS_ENOMEM
+        assert not out.any()
+        assert srv.stats()["error"] == hgrms.HGRMS_ENOMEM
+        srv.fail_allocations(2)
+        srv.fail_allocations(0)
+        for img, (ref, k_ref, _) in zip(imgs, refs):
+            out = np.empty_like(img)
+            k, _ = srv.wait(srv.submit(img, 10, 1, 32, out=out))
+            assert k == k_ref and np.array_equal(out, ref)
+
+
 def test_argument_errors(torch_cuda):
     from paper_1306_5390_gb300 import hgrms
     lib = hgrms.load_library()
