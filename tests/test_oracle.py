@@ -107,6 +107,59 @@ def test_exhaustive_3x3_literal_vs_gather(oracle_mod):
             assert np.array_equal(lit, out)
 
 
+def _direct_pass_4x4(imgs, alpha):
+    """One pass of Algorithms 1-2 (beta 1) on a stack of 4 x 4 images, by
+    the definitions: the four interior pixels each read their 3 x 3 window
+    of the previous image (Section 2's temporary image and copy-back);
+    card counts |I_n - I_p| < alpha, and for card <= 2 a window value is
+    open unless I_p - alpha < I_n <= I_p + alpha; flag > 9 - 3 replaces the
+    pixel by floor(sqrt(floor(sum / flag)))."""
+    old = imgs.astype(np.int64)
+    out = old.copy()
+    for y in (1, 2):
+        for x in (1, 2):
+            p = old[:, y, x][:, None]
+            win = old[:, y - 1:y + 2, x - 1:x + 2].reshape(len(old), 9)
+            card = ((win > p - alpha) & (win < p + alpha)).sum(axis=1)
+            opn = ~((win > p - alpha) & (win <= p + alpha))
+            flag = opn.sum(axis=1)
+            ssum = (win * win * opn).sum(axis=1)
+            q = ssum // np.maximum(flag, 1)
+            r = np.floor(np.sqrt(q.astype(np.float64))).astype(np.int64)
+            r -= (r * r > q)
+            r += ((r + 1) * (r + 1) <= q)
+            rep = (card <= 2) & (flag > 6)
+            out[:, y, x] = np.where(rep, r, old[:, y, x])
+    return out.astype(np.uint8)
+
+
+def test_sampled_4x4_against_the_direct_definition(oracle_mod):
+    """4 x 4 images (the smallest whose interior windows overlap, so a pass
+    that updated pixels in place would differ), 8,000 per palette and alpha
+    drawn from 3^16: the oracle's iteration (bytes, k, converged; max_k 4)
+    equals iterating the direct definition with the stop rule of Section 2
+    (k = passes that changed a pixel, stopping after the first that changes
+    none)."""
+    rng = np.random.Generator(np.random.PCG64(4416))
+    palettes = [(0, 100, 255), (100, 110, 90), (0, 5, 10)]
+    max_k = 4
+    for pal, alpha in itertools.product(palettes, (0, 1, 10, 100)):
+        imgs = np.asarray(pal, dtype=np.uint8)[rng.integers(0, 3, size=(8000, 4, 4))]
+        cur = imgs.copy()
+        k = np.zeros(len(imgs), dtype=np.int64)
+        done = np.zeros(len(imgs), dtype=bool)
+        for _ in range(max_k):
+            nxt = _direct_pass_4x4(cur, alpha)
+            changed = (nxt != cur).reshape(len(cur), -1).any(axis=1)
+            done |= ~changed
+            k += changed & ~done
+            cur = np.where(done[:, None, None], cur, nxt)
+        for i in range(len(imgs)):
+            out, k_o, conv = oracle_mod.denoise(imgs[i], alpha, 1, max_k)
+            assert (k_o, conv) == (int(k[i]), bool(done[i])), (pal, alpha, imgs[i].tolist())
+            assert np.array_equal(out, cur[i]), (pal, alpha, imgs[i].tolist())
+
+
 @pytest.mark.parametrize("beta", [1, 2, 3, 4, 7])
 def test_literal_loop_equals_gather_loop_random(oracle_mod, beta):
     for seed in range(6):
