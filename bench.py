@@ -337,7 +337,10 @@ def run_ours(args, rank, world, local):
     pix_iters_per_step = units / max(1, args.steps) / world
     step_s = total_ms * 1e-3 / args.steps
     hbm_eff = 2.0 * pix_iters_per_step / step_s / 1e9
-    launches = sum(acc[b]["launches"] + 3 * acc[b]["calls"] for b in betas)  # + init, tile map, copy-out
+    # Denoising launches plus the control-block init and the copy-out of
+    # every call (the tile-map kernel runs only when a handle's layout
+    # changes: in the warm-up, not in the timed steps).
+    launches = sum(acc[b]["launches"] + 2 * acc[b]["calls"] for b in betas)
 
     out = {
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
@@ -632,8 +635,10 @@ def batch_section(torch, local, args):
                       "tuning_ms": round(tune_ms, 1)},
         "identical_outputs_and_k": same,
         "l2": f"{L2_FLUSH_BYTES >> 20} MiB buffer written before every timed step",
-        # copies in and out, table upload, tile map, control init, fused, list loop
-        "_launches": int(st["launches"]) + 4,
+        # the denoising launches, control init and the batched copy-out (one
+        # chunk at this size; device images need no copy-in, and the table
+        # and tile map are unchanged after the first call)
+        "_launches": int(st["launches"]) + 2,
     }
 
 
