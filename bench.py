@@ -130,8 +130,16 @@ class ClockSampler:
         self.gpu = gpu_index
         self.proc = None
         self.file = None
+        self.skip = 0
 
-    def start(self):
+    def _lines(self):
+        with open(self.file.name) as f:
+            return [ln for ln in f if ln.strip()]
+
+    def start(self, wait_s: float = 3.0):
+        """Start sampling every 25 ms and wait (at most wait_s) for the
+        first sample; the samples written before start() returns are
+        skipped, so the ones kept are taken during the timed steps."""
         try:
             self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
@@ -140,6 +148,14 @@ class ClockSampler:
                 stdout=self.file, stderr=subprocess.DEVNULL)
         except (OSError, FileNotFoundError):
             self.proc = None
+            return
+        t0 = time.time()
+        while time.time() - t0 < wait_s and self.proc.poll() is None:
+            n = len(self._lines())
+            if n:
+                self.skip = n
+                break
+            time.sleep(0.005)
 
     def stop(self):
         if self.proc is None:
@@ -149,11 +165,13 @@ class ClockSampler:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
-        self.file.flush()
-        self.file.seek(0)
-        rows = [ln.strip().split(",") for ln in self.file if ln.strip()]
+        lines = self._lines()
         self.file.close()
         os.unlink(self.file.name)
+        # The samples taken after start() returned (the last one if the
+        # region was shorter than the sampling period).
+        kept = lines[self.skip:] if len(lines) > self.skip else lines[-1:]
+        rows = [ln.strip().split(",") for ln in kept]
         sm, smax, reasons = [], [], set()
         names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
         for r in rows:
